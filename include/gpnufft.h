@@ -1,0 +1,185 @@
+/* gpnufft.h -- C ABI of the GB300 (sm_103a) NUFFT-based GP matvec and solve.
+ *
+ * Method: Kielstra & Lindsey, "Gaussian process regression with log-linear
+ * scaling for common non-stationary kernels" (arXiv 2407.03608).
+ *
+ * The library applies the approximate kernel matrix K~ of Eq. (Ktilde) (Sec. 3.5)
+ * to vectors through the five steps of Sec. 4.2:
+ *   (1) per-point Chebyshev weights c_k = w_k(x_i) alpha_i        (Eq. c, Eq. Wk)
+ *   (2) N_sigma+1 type-1 NUFFTs onto the Fourier grid            (App. D)
+ *   (3) a_k' = sum_j v~_j G^_k',j sum_k G^_k,j b_k  (precomputed A, Remark rem:step3)
+ *   (4) N_sigma+1 type-2 NUFFTs back to the points                (App. D)
+ *   (5) sum_k w_k(x_i) beta_k
+ * and wraps it in conjugate gradients for (K + eta^2 I) alpha = y (Eq. gprsolve).
+ *
+ * Kernel (Sec. 3, Eq. nonstat2):
+ *   K(x,y) = w(x) w(y) (2 pi [sigma^2(x)+sigma^2(y)])^(-d/2) phi(|x-y| / sqrt(sigma^2(x)+sigma^2(y)))
+ * with phi the Matern function of Eq. (matern) or the squared exponential of
+ * Eq. (squaredexp).  By default the two per-point fields are the vertical scale
+ * s(x) and the Matern length l(x); the library converts them with
+ *   sigma(x) = l(x)/sqrt(2),  w(x) = s(x) (2 pi)^(d/4) l(x)^(d/2),
+ * which makes Eq. (nonstat2) the Paciorek non-stationary Matern with
+ * K(x,x) = s(x)^2.  GP_PARAMS_PAPER passes w(x) and sigma(x) directly.
+ *
+ * Conventions for every entry point:
+ *  - Return value is a gp_status; 0 is success.  No C++ exception and no exit()
+ *    crosses the ABI.  gp_last_error() returns a message for the calling thread.
+ *  - Pointers may be device pointers (cudaMalloc / torch CUDA tensors, on the
+ *    plan's device) or host pointers (pageable or pinned).  The library detects
+ *    which with cudaPointerGetAttributes.  Device pointers are used in place and
+ *    the call is stream ordered: it returns before the work is done, and the
+ *    inputs must stay valid until the stream passes the call.  For host
+ *    pointers the library copies through its own device staging buffers and
+ *    synchronises the stream before returning, so results are ready on return.
+ *  - Floating-point data crosses the ABI in float64 whatever the plan's
+ *    internal precision.
+ *  - Vectors with R right-hand sides are N x R column-major (column r starts at
+ *    element r*N), in the caller's original point order.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ *  - A plan owns all device memory it allocates and frees it in gp_destroy.
+ *    Calls on one plan must not overlap on different streams or threads.
+ */
+#ifndef GPNUFFT_H
+#define GPNUFFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_plan_s* gp_plan_t;
+
+typedef enum {
+  GP_OK = 0,
+  GP_EINVAL = -1,        /* invalid argument (message in gp_last_error)            */
+  GP_ENOMEM = -2,        /* device allocation failed or plan exceeds opts.max_bytes */
+  GP_ECUDA = -3,         /* CUDA runtime error                                       */
+  GP_ECUFFT = -4,        /* cuFFT error                                              */
+  GP_ENOTCONV = -5,      /* CG reached maxit before rtol; alpha holds the last iterate */
+  GP_EBREAKDOWN = -6,    /* CG breakdown: p^T A p <= 0 or not finite                 */
+  GP_ETIMEOUT = -7,      /* a bounded device wait ran out                            */
+  GP_EUNSUPPORTED = -8   /* configuration not supported by this build                */
+} gp_status;
+
+enum { GP_FP64 = 0, GP_FP32 = 1 };                 /* arithmetic of spread/FFT/step 3/interp */
+enum { GP_MATERN = 0, GP_SE = 1 };                 /* phi: Eq. (matern) or Eq. (squaredexp)   */
+enum { GP_PARAMS_SCALES = 0, GP_PARAMS_PAPER = 1 };/* fields are (s, l) or (w, sigma)         */
+
+/* Bits of gp_plan_opts.set: which override fields are valid.  Zero = all
+ * hyperparameters chosen from eps (Sec. 5.4 recipe with numeric stage estimates). */
+enum {
+  GP_SET_NT = 1u << 0,        /* n_t, t_min, t_max           (Eq. dtscheme)          */
+  GP_SET_NSIGMA = 1u << 1,    /* n_sigma                     (Eq. chebscheme)        */
+  GP_SET_SIGMA_RANGE = 1u << 2,/* sigma_lo, sigma_hi (paper sigma, not l)            */
+  GP_SET_M = 1u << 3,         /* M: Fourier grid {-M..M}^d   (Sec. 3.4)              */
+  GP_SET_DW = 1u << 4,        /* dw: Fourier grid spacing    (Sec. 3.4)              */
+  GP_SET_NUFFT = 1u << 5,     /* nufft_tol, upsampfac        (App. D)                */
+  GP_SET_BOX = 1u << 6,       /* box_lo, box_hi: region all points and queries lie in */
+  GP_SET_NF = 1u << 7,        /* nf: fine-grid size per dimension (FFT length)        */
+  GP_SET_TILE = 1u << 8       /* tile: spread/interp tile edge in fine-grid cells     */
+};
+
+typedef struct gp_plan_opts {
+  int precision;          /* GP_FP64 (default) or GP_FP32                               */
+  int family;             /* GP_MATERN (default) or GP_SE (nu ignored)                  */
+  int param_mode;         /* GP_PARAMS_SCALES (default) or GP_PARAMS_PAPER              */
+  unsigned set;           /* GP_SET_* bits                                              */
+  int n_t; double t_min, t_max;
+  int n_sigma; double sigma_lo, sigma_hi;
+  long long M; double dw;
+  double nufft_tol; double upsampfac;
+  double box_lo[3], box_hi[3];
+  long long nf;
+  int tile;
+  int max_rhs;            /* largest R the plan will be called with (default 1)         */
+  long long max_bytes;    /* refuse plans whose resident device bytes exceed this (0 = no limit) */
+} gp_plan_opts;
+
+typedef struct gp_plan_info {
+  int d; long long N; int family; int precision; double nu; double eps;
+  int n_t; double t_min, t_max;            /* trapezoid rule in t (Eq. dtscheme)          */
+  int n_sigma; double sigma_lo, sigma_hi;  /* Chebyshev-Lobatto interval (Eq. chebscheme) */
+  long long M; double dw;                  /* Fourier grid n dw, n in {-M..M}^d           */
+  long long nf;                            /* fine grid per dimension (FFT length)        */
+  int kernel_width; double kernel_beta;    /* exponential-of-semicircle spreading kernel  */
+  double upsampfac; double nufft_tol;
+  int tile;                                /* spread/interp tile edge (cells)             */
+  double box_lo[3], box_hi[3];             /* region points and queries must lie in       */
+  double est_err_t, est_err_sigma, est_err_trunc, est_err_alias; /* stage estimates, relative entrywise */
+  long long bytes_resident;                /* device bytes the plan holds                 */
+  int max_rhs;
+} gp_plan_info;
+
+/* Fill opts with the defaults (all zero except max_rhs = 1). */
+void gp_plan_opts_default(gp_plan_opts* opts);
+
+/* Build a plan for the N points x_i in R^d.
+ *   points : N x d row-major float64 (host or device).
+ *   field_a, field_b : N float64 each. GP_PARAMS_SCALES: s(x_i) > 0 and l(x_i) > 0.
+ *                      GP_PARAMS_PAPER: w(x_i) >= 0 and sigma(x_i) > 0 (Eq. nonstat2).
+ *   nu  : Matern smoothness > 0 (Eq. matern); ignored for GP_SE.
+ *   eps : target entrywise error of K~ relative to sqrt(K_ii K_jj) (Theorem main),
+ *         in (0, 0.1].  It drives every hyperparameter that opts does not set.
+ * Builds the quadrature in t (Sec. 3.2), the Chebyshev nodes (Sec. 3.3), the Fourier
+ * grid (Sec. 3.4), sorts the points into fine-grid tiles, and precomputes the
+ * per-point weights w_k(x_i) (Eq. Wk) and the tensor A[n] (Remark rem:step3).
+ * Errors: GP_EINVAL (d not 1..3, N < 1, nu <= 0, eps out of range, non-positive
+ * scale, inconsistent overrides), GP_ENOMEM, GP_ECUDA, GP_ECUFFT. On error *out is NULL. */
+int gp_plan(gp_plan_t* out, const double* points, long long N, int d, const double* field_a,
+            const double* field_b, double nu, double eps, const gp_plan_opts* opts, void* cuda_stream);
+
+/* out = (K~ + shift I) alpha for R right-hand sides (steps (1)-(5) of Sec. 4.2).
+ *   alpha, out : N x R column-major float64 (host or device; may not alias).
+ *   R : 1 <= R <= opts.max_rhs of the plan.
+ * Errors: GP_EINVAL, GP_ECUDA, GP_ECUFFT. */
+int gp_matvec(gp_plan_t plan, const double* alpha, double* out, int R, double shift, void* cuda_stream);
+
+/* Solve (K~ + eta2 I) alpha = y (Eq. gprsolve) by conjugate gradients, each column
+ * independently, all columns sharing each matvec launch.  x0 = 0; column r stops
+ * when ||r_k|| / ||y_r|| <= rtol (recurrence residual).
+ *   y, alpha : N x R column-major float64 (host or device).
+ *   iters_out, relres_out : R entries each (host pointers, may be NULL): iterations
+ *              taken and final recurrence relative residual per column.
+ * CG scalars and reductions are float64 whatever the plan precision.
+ * Errors: GP_EINVAL, GP_ENOTCONV (alpha holds the last iterate), GP_EBREAKDOWN,
+ * GP_ECUDA, GP_ECUFFT. */
+int gp_cg_solve(gp_plan_t plan, const double* y, double* alpha, int R, double eta2, double rtol, int maxit,
+                int* iters_out, double* relres_out, void* cuda_stream);
+
+/* Mixed-precision solve: CG with the matvec of plan_lo (normally GP_FP32) inside an
+ * outer iterative-refinement loop whose residual y - (K~ + eta2 I) alpha is
+ * recomputed with plan_hi (normally GP_FP64).  Both plans must have been built
+ * on the same points and fields with identical hyperparameters (pass plan_hi's
+ * gp_plan_info values as overrides when building plan_lo).  Stops when the
+ * plan_hi relative residual is <= rtol.  inner_rtol is the relative reduction each
+ * inner CG asks for; outer_max bounds the refinement steps.
+ *   iters_out : total inner CG iterations per column; relres_out : final plan_hi
+ *   relative residual per column.  Errors as gp_cg_solve. */
+int gp_cg_solve_refined(gp_plan_t plan_lo, gp_plan_t plan_hi, const double* y, double* alpha, int R, double eta2,
+                        double rtol, double inner_rtol, int outer_max, int maxit, int* iters_out,
+                        double* relres_out, void* cuda_stream);
+
+/* Posterior mean mu(x_q) = sum_n alpha_n K~(x_q, x_n) (Eq. postmean) at Nq query points.
+ *   alpha : N float64 (training coefficients, original order).
+ *   xq : Nq x d row-major; field_aq, field_bq : the two scale fields at the queries, in
+ *        the plan's param_mode.  Queries must lie in the plan box and their sigma in
+ *        [sigma_lo, sigma_hi] (gp_plan_info), else GP_EINVAL.
+ *   mu : Nq float64. */
+int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, long long Nq, const double* field_aq,
+                      const double* field_bq, double* mu, void* cuda_stream);
+
+/* Copy the plan's chosen hyperparameters and sizes into *info. */
+int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info);
+
+/* Free everything the plan owns.  NULL is ignored. */
+void gp_destroy(gp_plan_t plan);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gp_last_error(void);
+
+/* Library version string. */
+const char* gp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPNUFFT_H */

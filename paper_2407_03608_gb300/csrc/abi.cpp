@@ -1,0 +1,497 @@
+// The C ABI of include/gpnufft.h: argument checks, host/device pointer handling,
+// plan construction, and the entry points.  No exception crosses the ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace gpn {
+
+namespace {
+thread_local std::string g_last_error;
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear: plain host memory on some drivers
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Temporary device buffer freed at scope exit.
+struct DevTmp {
+  void* p = nullptr;
+  explicit DevTmp(size_t bytes) {
+    if (bytes && cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      fail(GP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " temporary bytes failed");
+    }
+  }
+  ~DevTmp() {
+    if (p) cudaFree(p);
+  }
+  DevTmp(const DevTmp&) = delete;
+  DevTmp& operator=(const DevTmp&) = delete;
+};
+
+// A device view of caller data: used in place when already on the device.
+struct DevIn {
+  const double* ptr = nullptr;
+  std::unique_ptr<DevTmp> tmp;
+  DevIn(const double* src, size_t count, cudaStream_t st) {
+    if (is_device_ptr(src)) {
+      ptr = src;
+      return;
+    }
+    tmp.reset(new DevTmp(sizeof(double) * std::max<size_t>(count, 1)));
+    GPN_CUDA(cudaMemcpyAsync(tmp->p, src, sizeof(double) * count, cudaMemcpyHostToDevice, st));
+    ptr = (const double*)tmp->p;
+  }
+};
+
+void* plan_alloc_cb(void* ctx, size_t bytes) { return static_cast<Plan*>(ctx)->alloc(bytes); }
+
+struct TmpList {
+  std::vector<void*> ptrs;
+  ~TmpList() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+void* tmp_alloc_cb(void* ctx, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(GP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  static_cast<TmpList*>(ctx)->ptrs.push_back(p);
+  return p;
+}
+
+int choose_tile(int d, int C, size_t rs, int width) {
+  static const int c1[] = {4096, 2048, 1024, 512, 256, 128, 64, 32, 16};
+  static const int c2[] = {64, 48, 32, 24, 16, 12, 8};
+  static const int c3[] = {16, 12, 10, 8, 6, 4};
+  const int* c = d == 1 ? c1 : (d == 2 ? c2 : c3);
+  int nc = d == 1 ? 9 : (d == 2 ? 7 : 6);
+  for (size_t budget : {size_t(96) << 10, size_t(200) << 10}) {
+    for (int i = 0; i < nc; ++i) {
+      size_t vol = 1;
+      for (int q = 0; q < d; ++q) vol *= c[i];
+      size_t smem = vol * C * rs + 8 * (rs * (kMaxDim * kMaxWidth + kMaxChannels));
+      if (smem <= budget && c[i] >= width - 1) return c[i];
+    }
+  }
+  fail(GP_EUNSUPPORTED, "no spreading tile fits in shared memory for these channels and kernel width");
+}
+
+int set_error(const Error& e) {
+  g_last_error = e.what();
+  return e.status;
+}
+
+template <class F>
+int guarded(F f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const Error& e) {
+    return set_error(e);
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return GP_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return GP_ECUDA;
+  } catch (...) {
+    g_last_error = "unknown internal error";
+    return GP_ECUDA;
+  }
+}
+
+Plan* as_plan(gp_plan_t p) {
+  GPN_CHECK(p != nullptr, GP_EINVAL, "null plan");
+  return reinterpret_cast<Plan*>(p);
+}
+
+void bind_device(const Plan& p) { GPN_CUDA(cudaSetDevice(p.device)); }
+
+}  // namespace
+
+void fail(int status, const std::string& msg) { throw Error(status, msg); }
+
+Plan::~Plan() {
+  for (auto& kv : fft_fwd) cufftDestroy(kv.second);
+  for (auto& kv : fft_inv) cufftDestroy(kv.second);
+  for (void* p : owned) cudaFree(p);
+  if (host_scal) cudaFreeHost(host_scal);
+}
+
+void* Plan::alloc(size_t nbytes) {
+  void* p = nullptr;
+  size_t b = std::max<size_t>(nbytes, 16);
+  if (cudaMalloc(&p, b) != cudaSuccess) {
+    cudaGetLastError();
+    fail(GP_ENOMEM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed (plan holds " + std::to_string(bytes) +
+                        ")");
+  }
+  owned.push_back(p);
+  bytes += (long long)b;
+  return p;
+}
+
+namespace {
+
+Plan* make_plan(const double* points, long long N, int d, const double* fa, const double* fb, double nu, double eps,
+                const gp_plan_opts& o, cudaStream_t st) {
+  GPN_CHECK(d >= 1 && d <= 3, GP_EINVAL, "d must be 1, 2 or 3");
+  GPN_CHECK(N >= 1, GP_EINVAL, "N must be >= 1");
+  GPN_CHECK(points && fa && fb, GP_EINVAL, "null points or fields");
+  GPN_CHECK(o.family == GP_MATERN || o.family == GP_SE, GP_EINVAL, "family must be GP_MATERN or GP_SE");
+  GPN_CHECK(o.family == GP_SE || (nu > 0.0 && std::isfinite(nu)), GP_EINVAL, "nu must be > 0");
+  GPN_CHECK(eps > 0.0 && eps <= 0.1, GP_EINVAL, "eps must be in (0, 0.1]");
+  GPN_CHECK(o.precision == GP_FP64 || o.precision == GP_FP32, GP_EINVAL, "precision must be GP_FP64 or GP_FP32");
+  GPN_CHECK(o.param_mode == GP_PARAMS_SCALES || o.param_mode == GP_PARAMS_PAPER, GP_EINVAL, "bad param_mode");
+  int max_rhs = o.max_rhs > 0 ? o.max_rhs : 1;
+  GPN_CHECK(max_rhs <= 1024, GP_EINVAL, "max_rhs must be <= 1024");
+
+  std::unique_ptr<Plan> plan(new Plan());
+  GPN_CUDA(cudaGetDevice(&plan->device));
+  plan->precision = o.precision;
+  plan->param_mode = o.param_mode;
+  plan->N = N;
+  plan->max_rhs = max_rhs;
+  plan->max_bytes = o.max_bytes;
+  plan->real_size = o.precision == GP_FP32 ? 4 : 8;
+
+  DevIn x(points, (size_t)N * d, st), a(fa, N, st), b(fb, N, st);
+  DevTmp wbuf(sizeof(double) * N), sbuf(sizeof(double) * N);
+  double* w = (double*)wbuf.p;
+  double* sig = (double*)sbuf.p;
+  fields_to_paper(a.ptr, b.ptr, w, sig, N, d, o.param_mode, st);
+  double stats[9];
+  field_stats(x.ptr, w, sig, N, d, stats, st);
+  GPN_CHECK(stats[8] == 0.0, GP_EINVAL,
+            std::to_string((long long)stats[8]) + " invalid entries (non-finite point, scale <= 0 or weight < 0)");
+
+  Hyper& h = plan->h;
+  h.d = d;
+  h.family = o.family;
+  h.nu = o.family == GP_SE ? INFINITY : nu;
+  h.eps = eps;
+  double smin = stats[0], smax = stats[1];
+  if (o.set & GP_SET_SIGMA_RANGE) {
+    GPN_CHECK(o.sigma_lo > 0.0 && o.sigma_hi >= o.sigma_lo, GP_EINVAL, "need 0 < sigma_lo <= sigma_hi");
+    GPN_CHECK(smin >= o.sigma_lo * (1 - 1e-12) && smax <= o.sigma_hi * (1 + 1e-12), GP_EINVAL,
+              "data sigma outside [sigma_lo, sigma_hi]");
+    h.sig_lo = o.sigma_lo;
+    h.sig_hi = o.sigma_hi;
+  } else if (smax - smin <= 1e-12 * smax) {
+    h.sig_lo = h.sig_hi = smax;
+  } else {
+    double pad = 0.01 * smax;
+    h.sig_lo = std::max(smin - pad, 0.5 * smin);
+    h.sig_hi = smax + pad;
+  }
+  for (int q = 0; q < d; ++q) {
+    double lo = stats[2 + q], hi = stats[5 + q];
+    if (o.set & GP_SET_BOX) {
+      GPN_CHECK(o.box_hi[q] > o.box_lo[q], GP_EINVAL, "box_hi must exceed box_lo");
+      GPN_CHECK(lo >= o.box_lo[q] && hi <= o.box_hi[q], GP_EINVAL, "points outside the given box");
+      h.box_lo[q] = o.box_lo[q];
+      h.box_hi[q] = o.box_hi[q];
+    } else {
+      double m = 1e-9 * std::max(hi - lo, 1e-3) + 1e-12;
+      h.box_lo[q] = lo - m;
+      h.box_hi[q] = hi + m;
+    }
+  }
+  select_hyper(h, o, o.precision, N);
+  const int C = h.n_sigma + 1;
+  h.tile = (o.set & GP_SET_TILE) ? o.tile : choose_tile(d, C, plan->real_size, h.width);
+  GPN_CHECK(h.tile >= h.width - 1 && h.tile >= 1, GP_EINVAL, "tile must be >= kernel width - 1");
+  build_tables(h, plan->tb);
+
+  GridGeom& g = plan->geom;
+  g.d = d;
+  g.nf = h.nf;
+  g.width = h.width;
+  g.beta = h.beta;
+  g.beta_f = (float)h.beta;
+  g.tile = h.tile;
+  g.C = C;
+  g.M = h.M;
+
+  // footprint check before the large allocations
+  const size_t rs = plan->real_size;
+  long long G = 1;
+  for (int q = 0; q < d; ++q) G *= h.nf;
+  long long S = G / h.nf * (h.nf / 2 + 1);
+  long long nfreq = 1;
+  for (int q = 0; q < d - 1; ++q) nfreq *= (2 * h.M + 1);
+  nfreq *= (h.M + 1);
+  plan->grid_elems = G;
+  plan->spec_elems = S;
+  plan->n_freq = nfreq;
+  long long est = (long long)(C * (long long)max_rhs * (G * rs + S * 2 * rs)) * 2  // grids + cuFFT work
+                  + (long long)(C * (C + 1) / 2) * nfreq * (long long)rs + N * (long long)(d * (4 + rs) + 4 + C * rs) +
+                  (long long)N * max_rhs * 8 * 9;
+  GPN_CHECK(o.max_bytes <= 0 || est <= o.max_bytes, GP_ENOMEM,
+            "plan needs about " + std::to_string(est) + " device bytes, above max_bytes");
+
+  build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get());
+  plan->a_tensor = plan->alloc((size_t)(C * (C + 1) / 2) * nfreq * rs);
+  build_a_tensor(*plan, st);
+  plan->grid = plan->alloc((size_t)C * max_rhs * G * rs);
+  plan->spec = plan->alloc((size_t)C * max_rhs * S * 2 * rs);
+  const size_t vb = sizeof(double) * (size_t)N * max_rhs;
+  plan->vec_a = (double*)plan->alloc(vb);
+  plan->vec_b = (double*)plan->alloc(vb);
+  plan->cg_x = (double*)plan->alloc(vb);
+  plan->cg_r = (double*)plan->alloc(vb);
+  plan->cg_p = (double*)plan->alloc(vb);
+  plan->cg_ap = (double*)plan->alloc(vb);
+  plan->cg_y = (double*)plan->alloc(vb);
+  plan->stage_in = (double*)plan->alloc(vb);
+  plan->stage_out = (double*)plan->alloc(vb);
+  plan->scal = (double*)plan->alloc(sizeof(double) * 8 * max_rhs);
+  plan->partials = (double*)plan->alloc(sizeof(double) * 512 * max_rhs);
+  GPN_CUDA(cudaMallocHost(&plan->host_scal, sizeof(double) * 8 * max_rhs));
+  plan->fwd_plan(1);
+  plan->inv_plan(1);
+  GPN_CUDA(cudaStreamSynchronize(st));
+  GPN_CHECK(plan->max_bytes <= 0 || plan->bytes <= plan->max_bytes, GP_ENOMEM, "plan exceeds max_bytes");
+  return plan.release();
+}
+
+// Resolve an output pointer: device pointers are written in place; host pointers go
+// through the plan's staging buffer and are copied back by finish().
+struct DevOut {
+  double* dev;
+  double* host = nullptr;
+  size_t count;
+  DevOut(double* dst, double* stage, size_t n) : dev(dst), count(n) {
+    if (!is_device_ptr(dst)) {
+      host = dst;
+      dev = stage;
+    }
+  }
+  void finish(cudaStream_t st) {
+    if (host) {
+      GPN_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+      GPN_CUDA(cudaStreamSynchronize(st));
+    }
+  }
+};
+
+// Input through the plan staging buffer when on the host.
+const double* dev_input(const double* src, double* stage, size_t count, cudaStream_t st) {
+  if (is_device_ptr(src)) return src;
+  GPN_CUDA(cudaMemcpyAsync(stage, src, sizeof(double) * count, cudaMemcpyHostToDevice, st));
+  return stage;
+}
+
+void check_same_hyper(const Plan& a, const Plan& b) {
+  const Hyper &x = a.h, &y = b.h;
+  bool same = a.N == b.N && x.d == y.d && x.family == y.family && x.n_t == y.n_t && x.t_min == y.t_min &&
+              x.t_max == y.t_max && x.n_sigma == y.n_sigma && x.sig_lo == y.sig_lo && x.sig_hi == y.sig_hi &&
+              x.M == y.M && x.dw == y.dw && (x.family == GP_SE || x.nu == y.nu);
+  GPN_CHECK(same, GP_EINVAL, "plan_lo and plan_hi must share points and hyperparameters");
+}
+
+}  // namespace
+}  // namespace gpn
+
+using namespace gpn;
+
+extern "C" {
+
+void gp_plan_opts_default(gp_plan_opts* opts) {
+  if (!opts) return;
+  std::memset(opts, 0, sizeof(*opts));
+  opts->max_rhs = 1;
+}
+
+int gp_plan(gp_plan_t* out, const double* points, long long N, int d, const double* field_a, const double* field_b,
+            double nu, double eps, const gp_plan_opts* opts, void* cuda_stream) {
+  if (out) *out = nullptr;
+  return guarded([&]() {
+    GPN_CHECK(out != nullptr, GP_EINVAL, "null output handle");
+    gp_plan_opts o;
+    gp_plan_opts_default(&o);
+    if (opts) o = *opts;
+    Plan* p = make_plan(points, N, d, field_a, field_b, nu, eps, o, (cudaStream_t)cuda_stream);
+    *out = reinterpret_cast<gp_plan_t>(p);
+    return GP_OK;
+  });
+}
+
+int gp_matvec(gp_plan_t plan, const double* alpha, double* out, int R, double shift, void* cuda_stream) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    GPN_CHECK(alpha && out, GP_EINVAL, "null alpha or out");
+    GPN_CHECK(R >= 1 && R <= p->max_rhs, GP_EINVAL, "R must be in [1, max_rhs]");
+    GPN_CHECK(std::isfinite(shift), GP_EINVAL, "shift must be finite");
+    const size_t cnt = (size_t)p->N * R;
+    const double* a = dev_input(alpha, p->stage_in, cnt, st);
+    DevOut o(out, p->stage_out, cnt);
+    gather_sorted(p->pts, a, p->vec_a, R, st);
+    matvec_sorted(*p, p->vec_a, p->vec_b, R, shift, st);
+    scatter_sorted(p->pts, p->vec_b, o.dev, R, st);
+    GPN_CUDA(cudaGetLastError());
+    o.finish(st);
+    return GP_OK;
+  });
+}
+
+int gp_cg_solve(gp_plan_t plan, const double* y, double* alpha, int R, double eta2, double rtol, int maxit,
+                int* iters_out, double* relres_out, void* cuda_stream) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    GPN_CHECK(y && alpha, GP_EINVAL, "null y or alpha");
+    GPN_CHECK(R >= 1 && R <= p->max_rhs, GP_EINVAL, "R must be in [1, max_rhs]");
+    GPN_CHECK(eta2 >= 0.0 && std::isfinite(eta2), GP_EINVAL, "eta2 must be >= 0");
+    GPN_CHECK(rtol > 0.0 && maxit >= 1, GP_EINVAL, "rtol > 0 and maxit >= 1 required");
+    const size_t cnt = (size_t)p->N * R;
+    const double* yd = dev_input(y, p->stage_in, cnt, st);
+    DevOut o(alpha, p->stage_out, cnt);
+    gather_sorted(p->pts, yd, p->cg_y, R, st);
+    int s = cg_solve_sorted(*p, p->cg_y, p->cg_x, R, eta2, rtol, maxit, iters_out, relres_out, st);
+    scatter_sorted(p->pts, p->cg_x, o.dev, R, st);
+    o.finish(st);
+    if (s == GP_ENOTCONV) g_last_error = "CG reached maxit before rtol";
+    if (s == GP_EBREAKDOWN) g_last_error = "CG breakdown (p^T A p <= 0 or not finite)";
+    return s;
+  });
+}
+
+int gp_cg_solve_refined(gp_plan_t plan_lo, gp_plan_t plan_hi, const double* y, double* alpha, int R, double eta2,
+                        double rtol, double inner_rtol, int outer_max, int maxit, int* iters_out, double* relres_out,
+                        void* cuda_stream) {
+  return guarded([&]() {
+    Plan* lo = as_plan(plan_lo);
+    Plan* hi = as_plan(plan_hi);
+    GPN_CHECK(lo != hi, GP_EINVAL, "plan_lo and plan_hi must differ");
+    GPN_CHECK(lo->device == hi->device, GP_EINVAL, "plans on different devices");
+    bind_device(*hi);
+    check_same_hyper(*lo, *hi);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    GPN_CHECK(y && alpha, GP_EINVAL, "null y or alpha");
+    GPN_CHECK(R >= 1 && R <= lo->max_rhs && R <= hi->max_rhs, GP_EINVAL, "R must be in [1, max_rhs] of both plans");
+    GPN_CHECK(eta2 >= 0.0 && rtol > 0.0 && inner_rtol > 0.0 && inner_rtol < 1.0 && outer_max >= 1 && maxit >= 1,
+              GP_EINVAL, "bad solver parameters");
+    const size_t cnt = (size_t)hi->N * R;
+    const double* yd = dev_input(y, hi->stage_in, cnt, st);
+    DevOut o(alpha, hi->stage_out, cnt);
+    gather_sorted(hi->pts, yd, hi->cg_y, R, st);
+    int s = cg_refined_sorted(*lo, *hi, hi->cg_y, hi->cg_x, R, eta2, rtol, inner_rtol, outer_max, maxit, iters_out,
+                              relres_out, st);
+    scatter_sorted(hi->pts, hi->cg_x, o.dev, R, st);
+    o.finish(st);
+    if (s == GP_ENOTCONV) g_last_error = "refinement reached outer_max before rtol";
+    return s;
+  });
+}
+
+int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, long long Nq, const double* field_aq,
+                      const double* field_bq, double* mu, void* cuda_stream) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    GPN_CHECK(alpha && xq && field_aq && field_bq && mu, GP_EINVAL, "null argument");
+    GPN_CHECK(Nq >= 1, GP_EINVAL, "Nq must be >= 1");
+    const int d = p->h.d;
+    DevIn x(xq, (size_t)Nq * d, st), a(field_aq, Nq, st), b(field_bq, Nq, st);
+    DevTmp wbuf(sizeof(double) * Nq), sbuf(sizeof(double) * Nq), outs(sizeof(double) * Nq), outo(sizeof(double) * Nq);
+    fields_to_paper(a.ptr, b.ptr, (double*)wbuf.p, (double*)sbuf.p, Nq, d, p->param_mode, st);
+    double stats[9];
+    field_stats(x.ptr, (double*)wbuf.p, (double*)sbuf.p, Nq, d, stats, st);
+    GPN_CHECK(stats[8] == 0.0, GP_EINVAL, "invalid query entries");
+    GPN_CHECK(stats[0] >= p->h.sig_lo * (1 - 1e-12) && stats[1] <= p->h.sig_hi * (1 + 1e-12), GP_EINVAL,
+              "query sigma outside the plan's [sigma_lo, sigma_hi]");
+    for (int q = 0; q < d; ++q)
+      GPN_CHECK(stats[2 + q] >= p->h.box_lo[q] && stats[5 + q] <= p->h.box_hi[q], GP_EINVAL,
+                "query points outside the plan box");
+    TmpList tl;
+    PointSet qs;
+    build_pointset(*p, qs, x.ptr, (double*)wbuf.p, (double*)sbuf.p, Nq, st, tmp_alloc_cb, &tl);
+    const double* al = dev_input(alpha, p->stage_in, (size_t)p->N, st);
+    gather_sorted(p->pts, al, p->vec_a, 1, st);
+    launch_spread(*p, p->vec_a, 1, st);
+    run_fft_forward(*p, 1, st);
+    launch_diag(*p, 1, st);
+    run_fft_inverse(*p, 1, st);
+    launch_interp(*p, qs, nullptr, 0.0, (double*)outs.p, 1, st);
+    DevOut o(mu, (double*)outo.p, (size_t)Nq);
+    scatter_sorted(qs, (double*)outs.p, o.dev, 1, st);
+    GPN_CUDA(cudaGetLastError());
+    o.finish(st);
+    GPN_CUDA(cudaStreamSynchronize(st));  // temporaries are freed on return
+    return GP_OK;
+  });
+}
+
+int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    GPN_CHECK(info != nullptr, GP_EINVAL, "null info");
+    const Hyper& h = p->h;
+    std::memset(info, 0, sizeof(*info));
+    info->d = h.d;
+    info->N = p->N;
+    info->family = h.family;
+    info->precision = p->precision;
+    info->nu = h.nu;
+    info->eps = h.eps;
+    info->n_t = h.n_t;
+    info->t_min = h.t_min;
+    info->t_max = h.t_max;
+    info->n_sigma = h.n_sigma;
+    info->sigma_lo = h.sig_lo;
+    info->sigma_hi = h.sig_hi;
+    info->M = h.M;
+    info->dw = h.dw;
+    info->nf = h.nf;
+    info->kernel_width = h.width;
+    info->kernel_beta = h.beta;
+    info->upsampfac = h.upsamp;
+    info->nufft_tol = h.nufft_tol;
+    info->tile = h.tile;
+    for (int q = 0; q < 3; ++q) {
+      info->box_lo[q] = h.box_lo[q];
+      info->box_hi[q] = h.box_hi[q];
+    }
+    info->est_err_t = h.est_t;
+    info->est_err_sigma = h.est_sigma;
+    info->est_err_trunc = h.est_trunc;
+    info->est_err_alias = h.est_alias;
+    info->bytes_resident = p->bytes;
+    info->max_rhs = p->max_rhs;
+    return GP_OK;
+  });
+}
+
+void gp_destroy(gp_plan_t plan) {
+  if (!plan) return;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  cudaSetDevice(p->device);
+  delete p;
+}
+
+const char* gp_last_error(void) { return g_last_error.c_str(); }
+
+const char* gp_version(void) { return "gpnufft 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

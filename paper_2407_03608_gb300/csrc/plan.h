@@ -1,0 +1,129 @@
+// Plan object: hyperparameters, device-resident point data, tables, grids and cuFFT plans.
+#pragma once
+
+#include <map>
+#include <vector>
+
+#include <cufft.h>
+
+#include "common.h"
+#include "params.h"
+
+namespace gpn {
+
+// Points binned into fine-grid tiles and sorted by tile (device memory).
+// A point's spreading support is the cells l0_a .. l0_a + width - 1 in each
+// dimension a; its bin is floor(l0_a / tile).  xi_a = g_a - l0_a where g_a is
+// the point's fine-grid coordinate.
+struct PointSet {
+  long long n = 0;
+  int nbins[kMaxDim] = {1, 1, 1};
+  long long nbins_total = 0;
+  int* cell0[kMaxDim] = {nullptr, nullptr, nullptr};   // l0_a, sorted order
+  void* xi[kMaxDim] = {nullptr, nullptr, nullptr};     // xi_a (real_t), sorted order
+  void* wk = nullptr;                                  // w_k(x_i) (real_t) [n][C]
+  int* perm = nullptr;                                 // sorted position -> caller index
+  int* bin_start = nullptr;                            // nbins_total + 1 offsets
+};
+
+// Launch parameters shared by the kernels.
+struct GridGeom {
+  int d;
+  long long nf;          // fine grid per dimension
+  int width;
+  float beta_f;
+  double beta;
+  int tile;
+  int C;                 // channels = n_sigma + 1
+  long long M;
+};
+
+struct Plan {
+  int device = 0;
+  int precision = GP_FP64;
+  int param_mode = GP_PARAMS_SCALES;
+  long long N = 0;
+  int max_rhs = 1;
+  long long max_bytes = 0;
+  Hyper h;
+  Tables tb;
+  GridGeom geom;
+  PointSet pts;
+  size_t real_size = 8;                 // sizeof(real_t)
+  // device buffers
+  void* a_tensor = nullptr;             // packed A'[p][f] (real_t), p < C(C+1)/2, f over the half box
+  long long n_freq = 0;                 // frequencies in the half box
+  void* grid = nullptr;                 // real fine grids, C * max_rhs * nf^d
+  void* spec = nullptr;                 // half spectra, C * max_rhs * nf^(d-1) * (nf/2+1) complex
+  long long grid_elems = 0, spec_elems = 0;   // per channel
+  double* vec_a = nullptr;              // sorted-order work vectors, N * max_rhs each
+  double* vec_b = nullptr;
+  double* cg_x = nullptr;               // CG state (sorted order)
+  double* cg_r = nullptr;
+  double* cg_p = nullptr;
+  double* cg_ap = nullptr;
+  double* cg_y = nullptr;
+  double* scal = nullptr;               // device scalars (see cg.cu)
+  double* partials = nullptr;           // reduction partials
+  double* host_scal = nullptr;          // pinned mirror
+  double* stage_in = nullptr;           // staging for host-pointer calls, N * max_rhs
+  double* stage_out = nullptr;
+  std::map<int, cufftHandle> fft_fwd, fft_inv;  // keyed by R
+  long long bytes = 0;
+  std::vector<void*> owned;             // every cudaMalloc of the plan
+
+  ~Plan();
+  void* alloc(size_t bytes);
+  cufftHandle fwd_plan(int R);
+  cufftHandle inv_plan(int R);
+};
+
+// ---- launchers (defined in the .cu files) ---------------------------------------
+
+// Bin and sort points given in caller order (device, row-major N x d), compute xi,
+// l0, bins, permutation, and the Chebyshev weights from the paper-native (w, sigma)
+// fields (device, caller order).  Allocates into ps through plan.alloc.
+// alloc(bytes) returns device memory owned by the caller of build_pointset.
+using DevAlloc = void* (*)(void* ctx, size_t bytes);
+void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double* w_dev, const double* sig_dev,
+                    long long n, cudaStream_t st, DevAlloc alloc, void* alloc_ctx);
+
+// Convert (s, l) to (w, sigma) in place (device, n entries), or validate (w, sigma).
+void fields_to_paper(const double* a, const double* b, double* w_out, double* sig_out, long long n, int d, int mode,
+                     cudaStream_t st);
+
+// min / max of sigma and of each coordinate, and the count of invalid entries.
+void field_stats(const double* x, const double* w, const double* sig, long long n, int d, double* host_out,
+                 cudaStream_t st);
+
+// Build the packed A' tensor on the device from the E' tables.
+void build_a_tensor(Plan& plan, cudaStream_t st);
+
+// Steps (1)+(2a): spread sorted-order coefficients alpha (N x R, float64) onto the
+// fine grids (C * R channels).
+void launch_spread(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st);
+// Steps (2b)+(3)+(4a): deconvolve, apply A', zero outside the mode box (in spec).
+void launch_diag(Plan& plan, int R, cudaStream_t st);
+// Steps (4b)+(5): interpolate at the points of ps and combine channels:
+// out[i] = sum_k w_k(x_i) beta_k(x_i) + shift * alpha_sorted[i] (alpha may be null).
+void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, double shift, double* out_sorted,
+                   int R, cudaStream_t st);
+// FFTs of the fine grids (forward R2C, inverse C2R), batched over C * R.
+void run_fft_forward(Plan& plan, int R, cudaStream_t st);
+void run_fft_inverse(Plan& plan, int R, cudaStream_t st);
+
+// Full matvec in sorted order: out = (K~ + shift I) alpha.
+void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st);
+
+// Permutations between caller order and sorted order (N x R column-major).
+void gather_sorted(const PointSet& ps, const double* src, double* dst, int R, cudaStream_t st);
+void scatter_sorted(const PointSet& ps, const double* src, double* dst, int R, cudaStream_t st);
+
+// CG in sorted order (cg.cu).
+int cg_solve_sorted(Plan& plan, const double* y_sorted, double* x_sorted, int R, double eta2, double rtol,
+                    int maxit, int* iters, double* relres, cudaStream_t st);
+int cg_refined_sorted(Plan& lo, Plan& hi, const double* y_sorted, double* x_sorted, int R, double eta2,
+                      double rtol, double inner_rtol, int outer_max, int maxit, int* iters, double* relres,
+                      cudaStream_t st);
+
+}  // namespace gpn
