@@ -1,0 +1,366 @@
+"""Benchmark of the non-stationary Matern GP hot path on one GB300 per rank.
+
+A step is one conjugate-gradient iteration on (K~ + eta^2 I) through the C ABI
+(gp_cg_solve): the matvec (spread, forward FFT, step 3, inverse FFT, interp) plus
+the float64 CG reductions and vector updates.  The metric is matvec throughput,
+points x right-hand sides per second (Mpts/s), on the 2-D clustered workload
+(N = 1e6: half uniform on the unit square, half in 8 Gaussian clusters, Matern
+nu = 3/2, eps = 1e-6).  Default path: FP32 spread/FFT/step 3/interp with float64
+CG; the plain float64 path is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (no collective on the data
+path); rank 0 prints one JSON line with the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NUFFT matvec Mpts/s (one CG iteration on K~ + eta^2 I), 2-D clustered N=1e6, Matern 3/2, eps=1e-6"
+UNIT = "Mpts/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--nu", type=float, default=1.5)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "of measured"
+    return 6800.0, "of fallback"
+
+
+# ------------------------------------------------------------------ workload
+def workload(args):
+    import gpinputs
+    w = gpinputs.config_2d(args.n, args.nu)
+    w.eps = args.eps
+    return w
+
+
+def algorithmic_bytes(info, N, R, rs):
+    """Algorithmic HBM bytes per launch of each matvec phase (reads + writes once)."""
+    d, nf, M = info["d"], info["nf"], info["M"]
+    C = info["n_sigma"] + 1
+    G = nf ** d
+    S = nf ** (d - 1) * (nf // 2 + 1)
+    nfreq = (2 * M + 1) ** (d - 1) * (M + 1)
+    L = max(info["box_hi"][a] - info["box_lo"][a] for a in range(d))
+    P = 1.0 / info["dw"]
+    occ = min(1.0, (L / P + (info["kernel_width"] + info["tile"]) / nf)) ** d
+    pts = N * (d * (4 + rs) + C * rs + 4)          # l0, xi, w_k, bin pointers
+    return {
+        "spread": C * R * G * rs + pts + N * R * 8,
+        "fft_fwd": C * R * (G * rs + S * 2 * rs),
+        "diag": C * R * nfreq * 2 * rs + (C * (C + 1) // 2) * nfreq * rs + C * R * S * 2 * rs,
+        "fft_inv": C * R * (S * 2 * rs + G * rs),
+        "interp": C * R * G * occ * rs + pts + 2 * N * R * 8,
+    }
+
+
+PHASES = ["spread", "fft_fwd", "diag", "fft_inv", "interp"]
+OUR_KERNELS_PER_STEP = 3 + 6   # spread, diag, interp + CG: dot partial/final, update_xr, final, update_p, roll
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2407_03608_gb300 as gpn
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = workload(args)
+    N = w.N
+    prec = gpn.GP_FP32 if args.precision == "fp32" else gpn.GP_FP64
+    eta2 = w.eta ** 2
+    pts = torch.from_numpy(w.points).to(dev)
+    s = torch.from_numpy(w.s).to(dev)
+    l = torch.from_numpy(w.l).to(dev)
+    y = torch.from_numpy(w.y).to(dev)
+    t0 = time.perf_counter()
+    plan = gpn.Plan(pts, s, l, nu=w.nu, eps=w.eps, precision=prec)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    info = plan.info
+    stream = torch.cuda.current_stream()
+    x = torch.empty_like(y)
+    from paper_2407_03608_gb300 import abi
+
+    def cg_steps(pl, k, yy, xx):
+        st, it, rel = abi.gp_cg_solve(pl.handle, yy, xx, 1, eta2, 1e-30, k)
+        return it[0]
+
+    # warm-up
+    cg_steps(plan, max(args.warmup, 1), y, x)
+    torch.cuda.synchronize()
+    # timed region: K CG iterations, events on the launching stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    abi.gp_profile_enable(plan.handle, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = cg_steps(plan, args.steps, y, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    phase_ms, n_rec = abi.gp_profile_read(plan.handle)
+    abi.gp_profile_enable(plan.handle, False)
+    clocks = sampler.stop()
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / iters
+    value = ws * N / (ms_step * 1e-3) / 1e6
+
+    # end to end through the public API with pinned host buffers: every step copies
+    # y in and alpha out (gp_cg_solve with host pointers runs one iteration per call)
+    yh = torch.from_numpy(w.y.copy()).pin_memory()
+    xh = torch.empty_like(yh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        abi.gp_cg_solve(plan.handle, yh, xh, 1, eta2, 1e-30, 1)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": ws * N / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
+           "ms_per_step": e2e_s * 1e3}
+
+    # accuracy of this path against the plain float64 GPU path on the same K~
+    ref64 = None
+    extra = {}
+    if prec == gpn.GP_FP32:
+        p64 = gpn.Plan(pts, s, l, nu=w.nu, eps=w.eps, precision=gpn.GP_FP64, **plan.matched_opts())
+        a = torch.from_numpy(w.alpha).to(dev)
+        o32 = plan.matvec(a)
+        o64 = p64.matvec(a)
+        err = float(torch.linalg.norm(o32 - o64) / torch.linalg.norm(o64))
+        x64 = torch.empty_like(y)
+        cg_steps(p64, 1, y, x64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        it64 = cg_steps(p64, args.fp64_steps, y, x64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / it64
+        extra["fp64_path"] = {"value": N / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64, "steps": it64}
+        extra["matvec_rel_err_vs_fp64_gpu"] = err
+        ref64 = o64.cpu().numpy()
+        p64.close()
+    out_sample = plan.matvec(torch.from_numpy(w.alpha).to(dev)).cpu().numpy()
+
+    rs = 4 if prec == gpn.GP_FP32 else 8
+    ab = algorithmic_bytes(info, N, 1, rs)
+    dom = max(range(5), key=lambda q: phase_ms[q])
+    ours = [0, 2, 4]
+    dom_ours = max(ours, key=lambda q: phase_ms[q])
+    peak, peak_src = measured_peaks()
+
+    def roof(q):
+        ach = ab[PHASES[q]] / (phase_ms[q] * 1e-3) / 1e9
+        return {"kernel": PHASES[q], "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes": int(ab[PHASES[q]]), "ms_per_launch": round(phase_ms[q], 4)}
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": iters,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == gpn.GP_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": N, "d": w.d, "nu": w.nu, "eps": w.eps, "R": 1,
+                   "precision": args.precision + (" spread/FFT/step3/interp, f64 CG" if prec == gpn.GP_FP32 else ""),
+                   "n_t": info["n_t"], "n_sigma": info["n_sigma"], "M": info["M"], "nf": info["nf"],
+                   "kernel_width": info["kernel_width"], "tile": info["tile"], "plan_seconds": round(plan_s, 3),
+                   "bytes_resident": info["bytes_resident"],
+                   "l2": "inputs larger than L2 (fine grids %.2f GB per pass)" % (
+                       (info["n_sigma"] + 1) * info["nf"] ** w.d * rs / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof(dom_ours),
+        "roofline_all": [roof(q) for q in range(5)],
+        "dominant_phase": PHASES[dom],
+        "phase_ms": {PHASES[q]: round(phase_ms[q], 4) for q in range(5)},
+        "phases_recorded": n_rec,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": OUR_KERNELS_PER_STEP * iters,
+    }
+    result.update(extra)
+    return result, w, out_sample, plan
+
+
+def cpu_baseline(w, gpu_out, seconds):
+    """The oracle's exact sampled rows of K alpha, timed on this host's cores."""
+    from oracle import kernel as okern
+    from oracle import rows as orows
+    orows.build()
+    wp, sig = okern.paper_fields(w.s, w.l, w.d)
+    rng = np.random.default_rng(123)
+    done, t_used, errs_num, errs_den = 0, 0.0, 0.0, 0.0
+    chunk = 64
+    while t_used < seconds:
+        idx = rng.integers(0, w.N, chunk)
+        t0 = time.perf_counter()
+        ref = orows.rows(w.points, wp, sig, w.nu, w.alpha, idx)
+        t_used += time.perf_counter() - t0
+        done += chunk
+        if gpu_out is not None:
+            errs_num += float(np.sum((gpu_out[idx] - ref) ** 2))
+            errs_den += float(np.sum(ref ** 2))
+    rows_per_s = done / t_used
+    res = {"value": rows_per_s / 1e6, "unit": UNIT, "cores": orows.threads_used(), "kind": "oracle",
+           "sample": "%d exact rows of K alpha by direct sum over N=%d (C, OpenMP), %.1f s; full step extrapolated "
+                     "as N rows" % (done, w.N, t_used)}
+    if gpu_out is not None:
+        res["gpu_rel_err_vs_oracle_rows"] = float(np.sqrt(errs_num / errs_den))
+    return res
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    w = workload(args)
+    from oracle import kernel as okern
+    from oracle import rows as orows
+    orows.build()
+    wp, sig = okern.paper_fields(w.s, w.l, w.d)
+    rng = np.random.default_rng(7)
+    per_step_rows = 128
+
+    def step():
+        orows.rows(w.points, wp, sig, w.nu, w.alpha, rng.integers(0, w.N, per_step_rows))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    # one step computes per_step_rows rows; a full CG step needs N rows
+    full_step_s = dt * w.N / per_step_rows
+    value = w.N / full_step_s / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": full_step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "N": w.N, "d": w.d, "nu": w.nu, "eps": w.eps, "R": 1},
+           "cpu_baseline": {"kind": "oracle", "cores": orows.threads_used(), "value": value, "unit": UNIT,
+                            "sample": "each step: %d exact rows of K alpha by direct sum over N=%d; full step "
+                                      "extrapolated as N rows" % (per_step_rows, w.N)},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    result, w, out_sample, plan = run_ours(args, ws, rank, local)
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(w, out_sample, args.cpu_seconds)
+        print(json.dumps(result), flush=True)
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

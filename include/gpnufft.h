@@ -167,6 +167,20 @@ int gp_cg_solve_refined(gp_plan_t plan_lo, gp_plan_t plan_hi, const double* y, d
 int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, long long Nq, const double* field_aq,
                       const double* field_bq, double* mu, void* cuda_stream);
 
+/* Per-phase timing of the matvec, with CUDA events recorded on the stream each
+ * phase is launched on.  gp_profile_enable(plan, 1) clears the counters and starts
+ * recording around every later matvec of this plan (gp_matvec, each CG iteration,
+ * posterior mean); gp_profile_enable(plan, 0) stops.  While recording, a matvec
+ * waits for the previous matvec's events before launching, so use it for
+ * measurement, not in production.  gp_profile_read writes the average
+ * milliseconds per launch into ms_avg[0..4]:
+ *   [0] spread (steps 1+2a)  [1] forward FFT  [2] step 3 (diag)  [3] inverse FFT
+ *   [4] interp (steps 4b+5)
+ * and the number of matvecs recorded into *count (may be NULL); it waits for the
+ * last recorded matvec.  Errors: GP_EINVAL, GP_ECUDA. */
+int gp_profile_enable(gp_plan_t plan, int on);
+int gp_profile_read(gp_plan_t plan, double* ms_avg, long long* count);
+
 /* Copy the plan's chosen hyperparameters and sizes into *info. */
 int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info);
 

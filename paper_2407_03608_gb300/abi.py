@@ -32,7 +32,8 @@ STATUS_NAMES = {0: "GP_OK", -1: "GP_EINVAL", -2: "GP_ENOMEM", -3: "GP_ECUDA", -4
 
 #: every symbol include/gpnufft.h declares
 EXPORTED = ["gp_plan_opts_default", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined",
-            "gp_posterior_mean", "gp_plan_info_get", "gp_destroy", "gp_last_error", "gp_version"]
+            "gp_posterior_mean", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
+            "gp_version"]
 
 
 class gp_plan_opts(ctypes.Structure):
@@ -88,6 +89,10 @@ def _load():
     lib.gp_cg_solve_refined.restype = ctypes.c_int
     lib.gp_posterior_mean.argtypes = [vp, dp, dp, ctypes.c_longlong, dp, dp, dp, vp]
     lib.gp_posterior_mean.restype = ctypes.c_int
+    lib.gp_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.gp_profile_enable.restype = ctypes.c_int
+    lib.gp_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    lib.gp_profile_read.restype = ctypes.c_int
     lib.gp_plan_info_get.argtypes = [vp, ctypes.POINTER(gp_plan_info)]
     lib.gp_plan_info_get.restype = ctypes.c_int
     lib.gp_destroy.argtypes = [vp]
@@ -210,6 +215,18 @@ def gp_posterior_mean(plan, alpha, xq, field_aq, field_bq, mu, stream=None):
     mp, mk = ptr_of(mu)
     return check(LIB.gp_posterior_mean(plan, ap, qp, int(xq.shape[0]), fa, fb, mp,
                                        stream if stream is not None else current_stream()))
+
+
+def gp_profile_enable(plan, on: bool):
+    return check(LIB.gp_profile_enable(plan, 1 if on else 0))
+
+
+def gp_profile_read(plan):
+    """(average ms per launch of [spread, fft_fwd, diag, fft_inv, interp], matvecs recorded)."""
+    ms = (ctypes.c_double * 5)()
+    cnt = ctypes.c_longlong()
+    check(LIB.gp_profile_read(plan, ms, ctypes.byref(cnt)))
+    return list(ms), cnt.value
 
 
 def gp_plan_info_get(plan) -> dict:

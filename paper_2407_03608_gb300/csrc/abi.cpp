@@ -128,6 +128,7 @@ void bind_device(const Plan& p) { GPN_CUDA(cudaSetDevice(p.device)); }
 void fail(int status, const std::string& msg) { throw Error(status, msg); }
 
 Plan::~Plan() {
+  prof.destroy();
   for (auto& kv : fft_fwd) cufftDestroy(kv.second);
   for (auto& kv : fft_inv) cufftDestroy(kv.second);
   for (void* p : owned) cudaFree(p);
@@ -439,6 +440,33 @@ int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, lon
     GPN_CUDA(cudaGetLastError());
     o.finish(st);
     GPN_CUDA(cudaStreamSynchronize(st));  // temporaries are freed on return
+    return GP_OK;
+  });
+}
+
+int gp_profile_enable(gp_plan_t plan, int on) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    if (on) {
+      p->prof.harvest();
+      for (double& a : p->prof.acc) a = 0.0;
+      p->prof.count = 0;
+    }
+    p->prof.on = on != 0;
+    return GP_OK;
+  });
+}
+
+int gp_profile_read(gp_plan_t plan, double* ms_avg, long long* count) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    GPN_CHECK(ms_avg != nullptr, GP_EINVAL, "null ms_avg");
+    p->prof.harvest();
+    long long n = p->prof.count;
+    for (int q = 0; q < 5; ++q) ms_avg[q] = n ? p->prof.acc[q] / n : 0.0;
+    if (count) *count = n;
     return GP_OK;
   });
 }

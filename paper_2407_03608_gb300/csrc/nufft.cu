@@ -557,12 +557,48 @@ void run_fft_inverse(Plan& plan, int R, cudaStream_t st) {
     GPN_CUFFT(cufftExecZ2D(h, (cufftDoubleComplex*)plan.spec, (cufftDoubleReal*)plan.grid));
 }
 
+void PhaseProfile::harvest() {
+  if (!pending) return;
+  GPN_CUDA(cudaEventSynchronize(ev[5]));
+  for (int q = 0; q < 5; ++q) {
+    float ms = 0.f;
+    GPN_CUDA(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
+    acc[q] += ms;
+  }
+  ++count;
+  pending = false;
+}
+
+void PhaseProfile::destroy() {
+  if (!created) return;
+  for (auto& e : ev) cudaEventDestroy(e);
+  created = false;
+}
+
 void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st) {
+  PhaseProfile& pf = plan.prof;
+  const bool rec = pf.on;
+  if (rec) {
+    pf.harvest();
+    if (!pf.created) {
+      for (auto& e : pf.ev) GPN_CUDA(cudaEventCreate(&e));
+      pf.created = true;
+    }
+    GPN_CUDA(cudaEventRecord(pf.ev[0], st));
+  }
   launch_spread(plan, alpha_sorted, R, st);
+  if (rec) GPN_CUDA(cudaEventRecord(pf.ev[1], st));
   run_fft_forward(plan, R, st);
+  if (rec) GPN_CUDA(cudaEventRecord(pf.ev[2], st));
   launch_diag(plan, R, st);
+  if (rec) GPN_CUDA(cudaEventRecord(pf.ev[3], st));
   run_fft_inverse(plan, R, st);
+  if (rec) GPN_CUDA(cudaEventRecord(pf.ev[4], st));
   launch_interp(plan, plan.pts, alpha_sorted, shift, out_sorted, R, st);
+  if (rec) {
+    GPN_CUDA(cudaEventRecord(pf.ev[5], st));
+    pf.pending = true;
+  }
 }
 
 }  // namespace gpn

@@ -38,8 +38,21 @@ struct GridGeom {
   long long M;
 };
 
+// Per-phase event timing of matvecs (diagnostic, off by default).
+struct PhaseProfile {
+  bool on = false;
+  bool created = false;
+  bool pending = false;
+  cudaEvent_t ev[6];
+  double acc[5] = {0, 0, 0, 0, 0};
+  long long count = 0;
+  void harvest();   // fold the pending event set into acc (waits for it)
+  void destroy();
+};
+
 struct Plan {
   int device = 0;
+  PhaseProfile prof;
   int precision = GP_FP64;
   int param_mode = GP_PARAMS_SCALES;
   long long N = 0;
