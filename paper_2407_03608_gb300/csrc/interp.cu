@@ -1,0 +1,257 @@
+// Steps (4b) + (5) of Sec. 4.2: interpolate the inverse-transformed fine grids at
+// the points (the type-2 NUFFTs of step (4) share this pass) and combine
+//   out_i = sum_k w_k(x_i) beta_k(x_i)  (+ shift * alpha_i).
+//
+// One CTA per (tile bin, right-hand side).  The bin's points need the cells
+// [b*tile, b*tile + tile + width - 1) in every dimension; the CTA stages that
+// block of every channel into shared memory with coalesced loads (in channel
+// chunks when it does not fit), then a group of lanes handles each point:
+//   d = 1: one lane per point;  d = 2: one lane per support row (width lanes);
+//   d = 3: one warp per point, lanes over the width^2 pencils.
+// Each lane accumulates its channels in registers and the group is reduced with
+// shuffles; the group leader applies the Chebyshev weights w_k(x_i) in float64.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace gpn {
+
+namespace {
+
+template <typename T>
+struct InterpArgs {
+  const int* cell0[kMaxDim];
+  const T* xi[kMaxDim];
+  const T* wk;
+  const int* bin_start;
+  int nbins[kMaxDim];
+  long long n;
+  const T* grid;
+  long long nf;
+  long long G;
+  int width;
+  T beta;
+  T inv_halfw;
+  int tile;
+  int ext;       // staged extent per dimension: tile + width - 1
+  int epitch;    // padded last-dimension pitch in shared memory
+  int cc;        // channels per staging chunk
+  int C;
+  const double* alpha;   // sorted order (may be null)
+  double shift;
+  double* out;           // sorted order, N x R
+};
+
+template <typename T, int D, int CMAX>
+__global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* st = reinterpret_cast<T*>(smem_raw);
+  const int p0 = a.bin_start[blockIdx.x], p1 = a.bin_start[blockIdx.x + 1];
+  if (p0 == p1) return;
+  const int npts = p1 - p0;
+  const int r = blockIdx.y, W = a.width, C = a.C, E = a.ext, EP = a.epitch;
+  int base[kMaxDim] = {0, 0, 0};
+  {
+    long long rest = blockIdx.x;
+#pragma unroll
+    for (int q = D - 1; q >= 0; --q) {
+      base[q] = (int)(rest % a.nbins[q]) * a.tile;
+      rest /= a.nbins[q];
+    }
+  }
+  int lead_e = 1;
+#pragma unroll
+  for (int q = 0; q < D - 1; ++q) lead_e *= E;
+  const int SV = lead_e * EP;  // staged volume per channel (padded)
+
+  constexpr int kGroup = D == 1 ? 1 : (D == 2 ? 0 : 32);  // 0: width lanes
+  const int Gs = kGroup == 0 ? W : kGroup;
+  const int ppw = 32 / Gs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int grp = lane / Gs, gl = lane - grp * Gs;
+  int P = 1;
+#pragma unroll
+  for (int q = 0; q < D - 1; ++q) P *= W;
+  const T* grid_r = a.grid + (size_t)r * C * a.G;
+  double* out_r = a.out + (size_t)r * a.n;
+  const double* alpha_r = a.alpha ? a.alpha + (size_t)r * a.n : nullptr;
+
+  for (int c0 = 0; c0 < C; c0 += a.cc) {
+    const int ncur = min(a.cc, C - c0);
+    __syncthreads();
+    // stage channels c0 .. c0+ncur-1 of the block
+    const int total = ncur * lead_e * E;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      int rem = idx;
+      const int last = rem % E;
+      rem /= E;
+      int soff = 0;
+      long long goff = 0;
+      bool in = (long long)base[D - 1] + last < a.nf;
+      int lcoord[kMaxDim];
+#pragma unroll
+      for (int q = D - 2; q >= 0; --q) {
+        lcoord[q] = rem % E;
+        rem /= E;
+      }
+      const int k = rem;
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) {
+        long long gq = (long long)base[q] + lcoord[q];
+        in = in && gq < a.nf;
+        soff = soff * E + lcoord[q];
+        goff = goff * a.nf + gq;
+      }
+      goff = goff * a.nf + base[D - 1] + last;
+      st[(size_t)k * SV + soff * EP + last] = in ? grid_r[(size_t)(c0 + k) * a.G + goff] : T(0);
+    }
+    __syncthreads();
+
+    for (int pb = warp * ppw; pb < npts; pb += nwarps * ppw) {
+      const int pi = pb + grp;
+      const bool active = grp < ppw && pi < npts;
+      T acc[CMAX];
+#pragma unroll
+      for (int k = 0; k < CMAX; ++k) acc[k] = T(0);
+      const int p = p0 + (active ? pi : 0);
+      if (active) {
+        int l0[kMaxDim];
+        T x[kMaxDim];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          l0[q] = a.cell0[q][p] - base[q];
+          x[q] = a.xi[q][p];
+        }
+        for (int pen = gl; pen < P; pen += Gs) {
+          int rem = pen, off = 0;
+          T plead = T(1);
+          int iq[kMaxDim];
+#pragma unroll
+          for (int q = D - 2; q >= 0; --q) {
+            iq[q] = rem % W;
+            rem /= W;
+          }
+#pragma unroll
+          for (int q = 0; q < D - 1; ++q) {
+            plead *= es_psi<T>((T)iq[q] - x[q], a.beta, a.inv_halfw);
+            off = off * E + l0[q] + iq[q];
+          }
+          const T* rowp = st + (size_t)off * EP + l0[D - 1];
+          for (int i = 0; i < W; ++i) {
+            const T wgt = plead * es_psi<T>((T)i - x[D - 1], a.beta, a.inv_halfw);
+#pragma unroll
+            for (int k = 0; k < CMAX; ++k)
+              if (k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+          }
+        }
+      }
+      // reduce within the point's lane group
+      if (kGroup == 32) {
+#pragma unroll
+        for (int k = 0; k < CMAX; ++k) {
+          if (k < ncur) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+          }
+        }
+      } else if (kGroup == 0) {
+#pragma unroll
+        for (int k = 0; k < CMAX; ++k) {
+          if (k < ncur) {
+            for (int o = 1; o < Gs; o <<= 1) {
+              T v = __shfl_down_sync(0xffffffffu, acc[k], o);
+              if (gl + o < Gs) acc[k] += v;
+            }
+          }
+        }
+      }
+      if (active && gl == 0) {
+        double res = 0.0;
+#pragma unroll
+        for (int k = 0; k < CMAX; ++k)
+          if (k < ncur) res += (double)a.wk[(size_t)p * C + c0 + k] * (double)acc[k];
+        if (c0 == 0) {
+          if (alpha_r) res += a.shift * alpha_r[p];
+          out_r[p] = res;
+        } else {
+          out_r[p] += res;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int D, int CMAX>
+void launch(const InterpArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+  GPN_CUDA(cudaFuncSetAttribute(k_interp<T, D, CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_interp<T, D, CMAX><<<grid, 256, smem, st>>>(a);
+}
+
+template <typename T, int D>
+void launch_c(const InterpArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+  switch (cmax_bucket(a.cc)) {
+    case 8: launch<T, D, 8>(a, grid, smem, st); break;
+    case 12: launch<T, D, 12>(a, grid, smem, st); break;
+    case 16: launch<T, D, 16>(a, grid, smem, st); break;
+    default: launch<T, D, 32>(a, grid, smem, st);
+  }
+}
+
+template <typename T>
+void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, double shift, double* out_sorted, int R,
+                 cudaStream_t st) {
+  const GridGeom& g = plan.geom;
+  InterpArgs<T> a{};
+  for (int q = 0; q < kMaxDim; ++q) {
+    a.cell0[q] = ps.cell0[q];
+    a.xi[q] = (const T*)ps.xi[q];
+    a.nbins[q] = ps.nbins[q];
+  }
+  a.wk = (const T*)ps.wk;
+  a.bin_start = ps.bin_start;
+  a.n = ps.n;
+  a.grid = (const T*)plan.grid;
+  a.nf = g.nf;
+  a.G = plan.grid_elems;
+  a.width = g.width;
+  a.beta = (T)g.beta;
+  a.inv_halfw = (T)(2.0 / g.width);
+  a.tile = g.tile;
+  a.ext = g.tile + g.width - 1;
+  a.epitch = g.d == 1 ? a.ext : (a.ext | 1);
+  a.C = g.C;
+  size_t per_ch = interp_stage_bytes(g.d, g.tile, g.width, sizeof(T));
+  a.cc = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.C, kInterpSmemBudget / per_ch));
+  a.alpha = alpha_sorted;
+  a.shift = shift;
+  a.out = out_sorted;
+  size_t smem = per_ch * a.cc;
+  dim3 grid((unsigned)ps.nbins_total, (unsigned)R);
+  switch (g.d) {
+    case 1: launch_c<T, 1>(a, grid, smem, st); break;
+    case 2: launch_c<T, 2>(a, grid, smem, st); break;
+    default: launch_c<T, 3>(a, grid, smem, st);
+  }
+  GPN_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+size_t interp_stage_bytes(int d, int tile, int width, size_t rs) {
+  size_t e = (size_t)tile + width - 1;
+  size_t lead = 1;
+  for (int q = 0; q < d - 1; ++q) lead *= e;
+  size_t pitch = d == 1 ? e : (e | 1);
+  return lead * pitch * rs;
+}
+
+void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, double shift, double* out_sorted,
+                   int R, cudaStream_t st) {
+  if (ps.n == 0) return;
+  if (plan.precision == GP_FP32)
+    interp_impl<float>(plan, ps, alpha_sorted, shift, out_sorted, R, st);
+  else
+    interp_impl<double>(plan, ps, alpha_sorted, shift, out_sorted, R, st);
+}
+
+}  // namespace gpn

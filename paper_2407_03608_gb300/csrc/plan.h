@@ -112,6 +112,13 @@ void field_stats(const double* x, const double* w, const double* sig, long long 
 // Build the packed A' tensor on the device from the E' tables.
 void build_a_tensor(Plan& plan, cudaStream_t st);
 
+// Shared-memory layout helpers of the spread / interp kernels.
+constexpr size_t kInterpSmemBudget = size_t(96) << 10;   // target when sizing channel chunks
+constexpr size_t kInterpSmemMax = size_t(200) << 10;      // one staged channel must fit
+int spread_pitch(int d, int tile);
+size_t spread_smem_bytes(int d, int tile, int C, size_t rs);
+size_t interp_stage_bytes(int d, int tile, int width, size_t rs);
+
 // Steps (1)+(2a): spread sorted-order coefficients alpha (N x R, float64) onto the
 // fine grids (C * R channels).
 void launch_spread(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st);

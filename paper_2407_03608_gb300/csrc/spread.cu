@@ -1,0 +1,218 @@
+// Steps (1) + (2a) of Sec. 4.2: spread c_k,i = w_k(x_i) alpha_i onto the fine grids,
+// for all Chebyshev channels k at once (the type-1 NUFFTs of step (2) share the
+// spreading pass).
+//
+// Output-stationary tiling.  One CTA owns one tile of tile^d fine-grid cells for
+// one right-hand side and accumulates, in shared memory, the contributions of
+// every point whose support meets the tile: with points binned by the first cell
+// of their support, those are the points of the 2^d bins at offsets {0,-1}^d.
+// The work is flattened over (point, pencil) pairs -- a pencil being the `width`
+// cells of a point's support along the last dimension -- so every thread stays
+// busy without warp-level synchronisation.  The tile is then written once with
+// coalesced stores: no global atomics and no pre-zeroing of the grid.
+// The shared tile's last dimension is padded to an odd pitch so that the rows a
+// warp touches fall in different banks.
+#include "kernels.h"
+
+namespace gpn {
+
+namespace {
+
+template <typename T>
+struct SpreadArgs {
+  const int* cell0[kMaxDim];
+  const T* xi[kMaxDim];
+  const T* wk;
+  const int* bin_start;
+  int nbins[kMaxDim];
+  const double* alpha;   // sorted order, N x R column-major
+  long long n;
+  T* grid;               // (R*C) x nf^d
+  long long nf;
+  long long G;           // nf^d
+  int width;
+  T beta;
+  T inv_halfw;
+  int tile;
+  int pitch;             // padded extent of the last tile dimension in shared memory
+  int C;
+};
+
+template <typename T, int D, int CMAX>
+__global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  const int TS = a.tile, TP = a.pitch, W = a.width, C = a.C;
+  int lead = 1;  // cells in the leading D-1 dimensions
+#pragma unroll
+  for (int q = 0; q < D - 1; ++q) lead *= TS;
+  const int TV = lead * TP;  // padded tile volume
+  const int r = blockIdx.y;
+
+  for (int i = threadIdx.x; i < C * TV; i += blockDim.x) tile[i] = T(0);
+
+  int tc[kMaxDim] = {0, 0, 0}, base[kMaxDim] = {0, 0, 0};
+  {
+    long long rest = blockIdx.x;
+#pragma unroll
+    for (int q = D - 1; q >= 0; --q) {
+      tc[q] = (int)(rest % a.nbins[q]);
+      rest /= a.nbins[q];
+      base[q] = tc[q] * TS;
+    }
+  }
+  __syncthreads();
+
+  int P = 1;  // pencils per point
+#pragma unroll
+  for (int q = 0; q < D - 1; ++q) P *= W;
+  const double* alpha_r = a.alpha + (size_t)r * a.n;
+
+#pragma unroll 1
+  for (int o = 0; o < (1 << D); ++o) {
+    long long lin = 0;
+    bool valid = true;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      int b = tc[q] - ((o >> q) & 1);
+      valid = valid && b >= 0;
+      lin = lin * a.nbins[q] + (b < 0 ? 0 : b);
+    }
+    if (!valid) continue;
+    const int p0 = a.bin_start[lin], p1 = a.bin_start[lin + 1];
+    const long long work = (long long)(p1 - p0) * P;
+    for (long long g = threadIdx.x; g < work; g += blockDim.x) {
+      const int pi = (int)(g / P);
+      int pen = (int)(g - (long long)pi * P);
+      const int p = p0 + pi;
+      // leading coordinates of this pencil and their tile-local cells
+      int off = 0;
+      bool inside = true;
+      T plead = T(1);
+      int iq[kMaxDim];
+#pragma unroll
+      for (int q = D - 2; q >= 0; --q) {
+        iq[q] = pen % W;
+        pen /= W;
+      }
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) {
+        int c = a.cell0[q][p] + iq[q] - base[q];
+        inside = inside && c >= 0 && c < TS;
+        off = off * TS + c;
+      }
+      const int l0 = a.cell0[D - 1][p];
+      const int lo = max(0, base[D - 1] - l0), hi = min(W, base[D - 1] + TS - l0);
+      if (!inside || lo >= hi) continue;
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) plead *= es_psi<T>((T)iq[q] - a.xi[q][p], a.beta, a.inv_halfw);
+      const T amp = plead * (T)alpha_r[p];
+      T s[CMAX];
+#pragma unroll
+      for (int k = 0; k < CMAX; ++k) s[k] = k < C ? a.wk[(size_t)p * C + k] * amp : T(0);
+      const T xl = a.xi[D - 1][p];
+      const int row = off * TP + (l0 - base[D - 1]);
+      for (int i = lo; i < hi; ++i) {
+        const T ps = es_psi<T>((T)i - xl, a.beta, a.inv_halfw);
+        T* cellp = tile + row + i;
+#pragma unroll
+        for (int k = 0; k < CMAX; ++k)
+          if (k < C) atomicAdd(cellp + (size_t)k * TV, ps * s[k]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // write the tile once (cells past nf in a partial last tile are dropped)
+  int vol = lead * TS;
+  for (int i = threadIdx.x; i < vol; i += blockDim.x) {
+    int rem = i;
+    long long gidx = 0, gstride = 1;
+    int sidx = 0, sstride = 1;
+    bool in = true;
+#pragma unroll
+    for (int q = D - 1; q >= 0; --q) {
+      int c = rem % TS;
+      rem /= TS;
+      long long gq = (long long)base[q] + c;
+      in = in && gq < a.nf;
+      gidx += gq * gstride;
+      gstride *= a.nf;
+      sidx += c * sstride;
+      sstride *= (q == D - 1) ? TP : TS;
+    }
+    if (!in) continue;
+    T* dst = a.grid + (size_t)r * C * a.G + gidx;
+#pragma unroll
+    for (int k = 0; k < CMAX; ++k)
+      if (k < C) dst[(size_t)k * a.G] = tile[(size_t)k * TV + sidx];
+  }
+}
+
+template <typename T, int D, int CMAX>
+void launch(const SpreadArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+  GPN_CUDA(cudaFuncSetAttribute(k_spread<T, D, CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_spread<T, D, CMAX><<<grid, 256, smem, st>>>(a);
+}
+
+template <typename T, int D>
+void launch_c(const SpreadArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+  switch (cmax_bucket(a.C)) {
+    case 8: launch<T, D, 8>(a, grid, smem, st); break;
+    case 12: launch<T, D, 12>(a, grid, smem, st); break;
+    case 16: launch<T, D, 16>(a, grid, smem, st); break;
+    default: launch<T, D, 32>(a, grid, smem, st);
+  }
+}
+
+template <typename T>
+void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
+  const GridGeom& g = plan.geom;
+  const PointSet& ps = plan.pts;
+  SpreadArgs<T> a{};
+  for (int q = 0; q < kMaxDim; ++q) {
+    a.cell0[q] = ps.cell0[q];
+    a.xi[q] = (const T*)ps.xi[q];
+    a.nbins[q] = ps.nbins[q];
+  }
+  a.wk = (const T*)ps.wk;
+  a.bin_start = ps.bin_start;
+  a.alpha = alpha_sorted;
+  a.n = ps.n;
+  a.grid = (T*)plan.grid;
+  a.nf = g.nf;
+  a.G = plan.grid_elems;
+  a.width = g.width;
+  a.beta = (T)g.beta;
+  a.inv_halfw = (T)(2.0 / g.width);
+  a.tile = g.tile;
+  a.pitch = spread_pitch(g.d, g.tile);
+  a.C = g.C;
+  size_t smem = spread_smem_bytes(g.d, g.tile, g.C, sizeof(T));
+  dim3 grid((unsigned)ps.nbins_total, (unsigned)R);
+  switch (g.d) {
+    case 1: launch_c<T, 1>(a, grid, smem, st); break;
+    case 2: launch_c<T, 2>(a, grid, smem, st); break;
+    default: launch_c<T, 3>(a, grid, smem, st);
+  }
+  GPN_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+int spread_pitch(int d, int tile) { return d == 1 ? tile : tile + 1; }
+
+size_t spread_smem_bytes(int d, int tile, int C, size_t rs) {
+  size_t lead = 1;
+  for (int q = 0; q < d - 1; ++q) lead *= tile;
+  return lead * spread_pitch(d, tile) * (size_t)C * rs;
+}
+
+void launch_spread(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
+  if (plan.precision == GP_FP32)
+    spread_impl<float>(plan, alpha_sorted, R, st);
+  else
+    spread_impl<double>(plan, alpha_sorted, R, st);
+}
+
+}  // namespace gpn
