@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "plan.h"
 
 namespace gpn {
@@ -135,6 +137,7 @@ Plan::~Plan() {
   for (auto& kv : fft_inv) cufftDestroy(kv.second);
   for (void* p : owned) cudaFree(p);
   if (host_scal) cudaFreeHost(host_scal);
+  if (host_status) cudaFreeHost(host_status);
 }
 
 void* Plan::alloc(size_t nbytes) {
@@ -150,7 +153,85 @@ void* Plan::alloc(size_t nbytes) {
   return p;
 }
 
+void check_device_status(Plan& plan, cudaStream_t st) {
+  GPN_CUDA(cudaMemcpyAsync(plan.host_status, plan.dev_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GPN_CUDA(cudaStreamSynchronize(st));
+  if (*plan.host_status != 0) {
+    *plan.host_status = 0;
+    GPN_CUDA(cudaMemsetAsync(plan.dev_status, 0, sizeof(int), st));
+    GPN_CUDA(cudaStreamSynchronize(st));
+    fail(GP_ETIMEOUT, "a device wait ran out (TMA copy did not complete); results of the call are invalid");
+  }
+}
+
 namespace {
+
+// Tiles that some point's support reaches: tile t gets the points of the bins at
+// offsets {0,-1}^d from it.
+void build_active_tiles(Plan& plan, const std::vector<int>& bstart) {
+  const PointSet& ps = plan.pts;
+  const int d = plan.h.d;
+  std::vector<int> act;
+  for (long long t = 0; t < ps.nbins_total; ++t) {
+    int tc[kMaxDim] = {0, 0, 0};
+    long long rest = t;
+    for (int q = d - 1; q >= 0; --q) {
+      tc[q] = (int)(rest % ps.nbins[q]);
+      rest /= ps.nbins[q];
+    }
+    bool any = false;
+    for (int o = 0; o < (1 << d) && !any; ++o) {
+      long long lin = 0;
+      bool valid = true;
+      for (int q = 0; q < d; ++q) {
+        int b = tc[q] - ((o >> q) & 1);
+        valid = valid && b >= 0;
+        lin = lin * ps.nbins[q] + (b < 0 ? 0 : b);
+      }
+      if (valid && bstart[lin + 1] > bstart[lin]) any = true;
+    }
+    if (any) act.push_back((int)t);
+  }
+  plan.n_active_tiles = (long long)act.size();
+  plan.active_tiles = (int*)plan.alloc(sizeof(int) * std::max<size_t>(act.size(), 1));
+  if (!act.empty())
+    GPN_CUDA(cudaMemcpy(plan.active_tiles, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice));
+}
+
+// TMA descriptor of the interp input grid: dims (nf, ..., nf, C * max_rhs), box =
+// (pitch, ext, ..., ext, interp_cc) so one copy stages a bin's block of cc channels.
+void make_tensor_map(Plan& plan) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    GPN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    GPN_CHECK(q == cudaDriverEntryPointSuccess && fn, GP_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const Hyper& h = plan.h;
+  const int d = h.d;
+  const size_t rs = plan.real_size;
+  const int ext = h.tile + h.width - 1;
+  cuuint64_t dims[4], strides[3];
+  cuuint32_t box[4], es[4] = {1, 1, 1, 1};
+  for (int q = 0; q < d; ++q) dims[q] = (cuuint64_t)h.nf;
+  dims[d] = (cuuint64_t)plan.geom.C * plan.max_rhs;
+  cuuint64_t st = rs;
+  for (int q = 0; q < d; ++q) {
+    st *= (cuuint64_t)h.nf;
+    strides[q] = st;
+  }
+  box[0] = (cuuint32_t)interp_pitch(d, h.tile, h.width, rs);
+  for (int q = 1; q < d; ++q) box[q] = (cuuint32_t)ext;
+  box[d] = (cuuint32_t)plan.interp_cc;
+  for (int q = 0; q <= d; ++q)
+    GPN_CHECK(box[q] >= 1 && box[q] <= 256, GP_EUNSUPPORTED, "TMA box dimension out of range");
+  CUresult r = encode(&plan.tmap_out, rs == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                      (cuuint32_t)(d + 1), plan.grid_out, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  GPN_CHECK(r == CUDA_SUCCESS, GP_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
 
 Plan* make_plan(const double* points, long long N, int d, const double* fa, const double* fb, double nu, double eps,
                 const gp_plan_opts& o, cudaStream_t st) {
@@ -243,17 +324,27 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->grid_elems = G;
   plan->spec_elems = S;
   plan->n_freq = nfreq;
-  long long est = (long long)(C * (long long)max_rhs * (G * rs + S * 2 * rs)) * 2  // grids + cuFFT work
+  long long est = (long long)(C * (long long)max_rhs * (2 * G * rs + S * 2 * rs)) * 2  // grids + cuFFT work
                   + (long long)(C * (C + 1) / 2) * nfreq * (long long)rs + N * (long long)(d * (4 + rs) + 4 + C * rs) +
                   (long long)N * max_rhs * 8 * 9;
   GPN_CHECK(o.max_bytes <= 0 || est <= o.max_bytes, GP_ENOMEM,
             "plan needs about " + std::to_string(est) + " device bytes, above max_bytes");
 
-  build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get());
+  std::vector<int> bstart;
+  build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
+  build_active_tiles(*plan, bstart);
   plan->a_tensor = plan->alloc((size_t)(C * (C + 1) / 2) * nfreq * rs);
   build_a_tensor(*plan, st);
   plan->grid = plan->alloc((size_t)C * max_rhs * G * rs);
+  GPN_CUDA(cudaMemsetAsync(plan->grid, 0, (size_t)C * max_rhs * G * rs, st));
+  plan->grid_out = plan->alloc((size_t)C * max_rhs * G * rs);
   plan->spec = plan->alloc((size_t)C * max_rhs * S * 2 * rs);
+  plan->interp_cc = (int)std::max<size_t>(
+      1, std::min<size_t>((size_t)C, kInterpSmemBudget / interp_stage_bytes(d, h.tile, h.width, rs)));
+  if (d >= 2) make_tensor_map(*plan);
+  plan->dev_status = (int*)plan->alloc(sizeof(int));
+  GPN_CUDA(cudaMemsetAsync(plan->dev_status, 0, sizeof(int), st));
+  GPN_CUDA(cudaMallocHost(&plan->host_status, sizeof(int)));
   const size_t vb = sizeof(double) * (size_t)N * max_rhs;
   plan->vec_a = (double*)plan->alloc(vb);
   plan->vec_b = (double*)plan->alloc(vb);
@@ -286,10 +377,10 @@ struct DevOut {
       dev = stage;
     }
   }
-  void finish(cudaStream_t st) {
+  void finish(Plan& plan, cudaStream_t st) {
     if (host) {
       GPN_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
-      GPN_CUDA(cudaStreamSynchronize(st));
+      check_device_status(plan, st);
     }
   }
 };
@@ -351,7 +442,7 @@ int gp_matvec(gp_plan_t plan, const double* alpha, double* out, int R, double sh
     matvec_sorted(*p, p->vec_a, p->vec_b, R, shift, st);
     scatter_sorted(p->pts, p->vec_b, o.dev, R, st);
     GPN_CUDA(cudaGetLastError());
-    o.finish(st);
+    o.finish(*p, st);
     return GP_OK;
   });
 }
@@ -372,7 +463,7 @@ int gp_cg_solve(gp_plan_t plan, const double* y, double* alpha, int R, double et
     gather_sorted(p->pts, yd, p->cg_y, R, st);
     int s = cg_solve_sorted(*p, p->cg_y, p->cg_x, R, eta2, rtol, maxit, iters_out, relres_out, st);
     scatter_sorted(p->pts, p->cg_x, o.dev, R, st);
-    o.finish(st);
+    o.finish(*p, st);
     if (s == GP_ENOTCONV) g_last_error = "CG reached maxit before rtol";
     if (s == GP_EBREAKDOWN) g_last_error = "CG breakdown (p^T A p <= 0 or not finite)";
     return s;
@@ -401,7 +492,7 @@ int gp_cg_solve_refined(gp_plan_t plan_lo, gp_plan_t plan_hi, const double* y, d
     int s = cg_refined_sorted(*lo, *hi, hi->cg_y, hi->cg_x, R, eta2, rtol, inner_rtol, outer_max, maxit, iters_out,
                               relres_out, st);
     scatter_sorted(hi->pts, hi->cg_x, o.dev, R, st);
-    o.finish(st);
+    o.finish(*hi, st);
     if (s == GP_ENOTCONV) g_last_error = "refinement reached outer_max before rtol";
     return s;
   });
@@ -440,8 +531,8 @@ int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, lon
     DevOut o(mu, (double*)outo.p, (size_t)Nq);
     scatter_sorted(qs, (double*)outs.p, o.dev, 1, st);
     GPN_CUDA(cudaGetLastError());
-    o.finish(st);
-    GPN_CUDA(cudaStreamSynchronize(st));  // temporaries are freed on return
+    o.finish(*p, st);
+    check_device_status(*p, st);  // temporaries are freed on return
     return GP_OK;
   });
 }
@@ -466,6 +557,7 @@ int gp_profile_read(gp_plan_t plan, double* ms_avg, long long* count) {
     bind_device(*p);
     GPN_CHECK(ms_avg != nullptr, GP_EINVAL, "null ms_avg");
     p->prof.harvest();
+    check_device_status(*p, nullptr);
     long long n = p->prof.count;
     for (int q = 0; q < 5; ++q) ms_avg[q] = n ? p->prof.acc[q] / n : 0.0;
     if (count) *count = n;

@@ -118,7 +118,7 @@ void dot(const double* u, const double* v, long long n, int R, double* partial, 
 void read_scalars(Plan& plan, int R, cudaStream_t st) {
   GPN_CUDA(cudaGetLastError());
   GPN_CUDA(cudaMemcpyAsync(plan.host_scal, plan.scal, sizeof(double) * 5 * R, cudaMemcpyDeviceToHost, st));
-  GPN_CUDA(cudaStreamSynchronize(st));
+  check_device_status(plan, st);
 }
 
 }  // namespace

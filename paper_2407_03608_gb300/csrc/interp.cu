@@ -2,14 +2,18 @@
 // the points (the type-2 NUFFTs of step (4) share this pass) and combine
 //   out_i = sum_k w_k(x_i) beta_k(x_i)  (+ shift * alpha_i).
 //
-// One CTA per (tile bin, right-hand side).  The bin's points need the cells
-// [b*tile, b*tile + tile + width - 1) in every dimension; the CTA stages that
-// block of every channel into shared memory with coalesced loads (in channel
-// chunks when it does not fit), then a group of lanes handles each point:
+// One CTA per non-empty tile bin and right-hand side.  The bin's points need the
+// cells [b*tile, b*tile + tile + width - 1) in every dimension.  For d >= 2 the
+// CTA brings that block of `cc` channels into shared memory with one TMA tile
+// copy (cp.async.bulk.tensor, completion on an mbarrier; out-of-range cells read
+// as zero); for d = 1 with a plain coalesced loop.  Then a group of lanes handles
+// each point:
 //   d = 1: one lane per point;  d = 2: one lane per support row (width lanes);
 //   d = 3: one warp per point, lanes over the width^2 pencils.
-// Each lane accumulates its channels in registers and the group is reduced with
-// shuffles; the group leader applies the Chebyshev weights w_k(x_i) in float64.
+// Each lane accumulates its channels in registers, the group is reduced with
+// shuffles, and the group leader applies the Chebyshev weights w_k(x_i) in float64.
+// The mbarrier wait is bounded: when it runs out the CTA records a timeout in the
+// plan's device status word and returns.
 #include <algorithm>
 
 #include "kernels.h"
@@ -18,12 +22,15 @@ namespace gpn {
 
 namespace {
 
+constexpr long long kMaxPolls = 1ll << 22;
+
 template <typename T>
 struct InterpArgs {
   const int* cell0[kMaxDim];
   const T* xi[kMaxDim];
   const T* wk;
   const int* bin_start;
+  const int* bins;       // non-empty bins
   int nbins[kMaxDim];
   long long n;
   const T* grid;
@@ -34,25 +41,28 @@ struct InterpArgs {
   T inv_halfw;
   int tile;
   int ext;       // staged extent per dimension: tile + width - 1
-  int epitch;    // padded last-dimension pitch in shared memory
+  int epitch;    // last-dimension pitch of the staged block in shared memory
   int cc;        // channels per staging chunk
   int C;
+  unsigned box_bytes;    // bytes of one TMA box
   const double* alpha;   // sorted order (may be null)
   double shift;
   double* out;           // sorted order, N x R
+  int* status;
 };
 
-template <typename T, int D, int CMAX>
-__global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* st = reinterpret_cast<T*>(smem_raw);
-  const int p0 = a.bin_start[blockIdx.x], p1 = a.bin_start[blockIdx.x + 1];
-  if (p0 == p1) return;
+template <typename T, int D, int CMAX, bool TMA>
+__global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+  T* st = reinterpret_cast<T*>(smem_raw + 128);
+  const int bin = a.bins[blockIdx.x];
+  const int p0 = a.bin_start[bin], p1 = a.bin_start[bin + 1];
   const int npts = p1 - p0;
   const int r = blockIdx.y, W = a.width, C = a.C, E = a.ext, EP = a.epitch;
   int base[kMaxDim] = {0, 0, 0};
   {
-    long long rest = blockIdx.x;
+    long long rest = bin;
 #pragma unroll
     for (int q = D - 1; q >= 0; --q) {
       base[q] = (int)(rest % a.nbins[q]) * a.tile;
@@ -62,7 +72,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a) {
   int lead_e = 1;
 #pragma unroll
   for (int q = 0; q < D - 1; ++q) lead_e *= E;
-  const int SV = lead_e * EP;  // staged volume per channel (padded)
+  const int SV = lead_e * EP;  // staged volume per channel
 
   constexpr int kGroup = D == 1 ? 1 : (D == 2 ? 0 : 32);  // 0: width lanes
   const int Gs = kGroup == 0 ? W : kGroup;
@@ -76,36 +86,57 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a) {
   double* out_r = a.out + (size_t)r * a.n;
   const double* alpha_r = a.alpha ? a.alpha + (size_t)r * a.n : nullptr;
 
+  if (TMA && threadIdx.x == 0) mbar_init(bar, 1);
+  unsigned phase = 0;
+
   for (int c0 = 0; c0 < C; c0 += a.cc) {
     const int ncur = min(a.cc, C - c0);
-    __syncthreads();
-    // stage channels c0 .. c0+ncur-1 of the block
-    const int total = ncur * lead_e * E;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      int rem = idx;
-      const int last = rem % E;
-      rem /= E;
-      int soff = 0;
-      long long goff = 0;
-      bool in = (long long)base[D - 1] + last < a.nf;
-      int lcoord[kMaxDim];
-#pragma unroll
-      for (int q = D - 2; q >= 0; --q) {
-        lcoord[q] = rem % E;
+    __syncthreads();  // the previous chunk has been read (and the barrier initialised)
+    if (TMA) {
+      if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, a.box_bytes);
+        if (D == 2)
+          tma_load_3d(st, &tmap, base[1], base[0], r * C + c0, bar);
+        else
+          tma_load_4d(st, &tmap, base[2], base[1], base[0], r * C + c0, bar);
+      }
+      const bool ok = mbar_wait_bounded(bar, phase, kMaxPolls);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          atomicExch(a.status, kStatusTimeout);
+          mbar_wait_bounded(bar, phase, kMaxPolls);  // let an in-flight copy land before exiting
+        }
+        return;
+      }
+      phase ^= 1u;
+    } else {
+      const int total = ncur * lead_e * E;
+      for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int rem = idx;
+        const int last = rem % E;
         rem /= E;
-      }
-      const int k = rem;
+        int soff = 0;
+        long long goff = 0;
+        bool in = (long long)base[D - 1] + last < a.nf;
+        int lcoord[kMaxDim];
 #pragma unroll
-      for (int q = 0; q < D - 1; ++q) {
-        long long gq = (long long)base[q] + lcoord[q];
-        in = in && gq < a.nf;
-        soff = soff * E + lcoord[q];
-        goff = goff * a.nf + gq;
+        for (int q = D - 2; q >= 0; --q) {
+          lcoord[q] = rem % E;
+          rem /= E;
+        }
+        const int k = rem;
+#pragma unroll
+        for (int q = 0; q < D - 1; ++q) {
+          const long long gq = (long long)base[q] + lcoord[q];
+          in = in && gq < a.nf;
+          soff = soff * E + lcoord[q];
+          goff = goff * a.nf + gq;
+        }
+        goff = goff * a.nf + base[D - 1] + last;
+        st[(size_t)k * SV + soff * EP + last] = in ? grid_r[(size_t)(c0 + k) * a.G + goff] : T(0);
       }
-      goff = goff * a.nf + base[D - 1] + last;
-      st[(size_t)k * SV + soff * EP + last] = in ? grid_r[(size_t)(c0 + k) * a.G + goff] : T(0);
+      __syncthreads();
     }
-    __syncthreads();
 
     for (int pb = warp * ppw; pb < npts; pb += nwarps * ppw) {
       const int pi = pb + grp;
@@ -159,7 +190,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a) {
         for (int k = 0; k < CMAX; ++k) {
           if (k < ncur) {
             for (int o = 1; o < Gs; o <<= 1) {
-              T v = __shfl_down_sync(0xffffffffu, acc[k], o);
+              const T v = __shfl_down_sync(0xffffffffu, acc[k], o);
               if (gl + o < Gs) acc[k] += v;
             }
           }
@@ -181,25 +212,27 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a) {
   }
 }
 
-template <typename T, int D, int CMAX>
-void launch(const InterpArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
-  GPN_CUDA(cudaFuncSetAttribute(k_interp<T, D, CMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_interp<T, D, CMAX><<<grid, 256, smem, st>>>(a);
+template <typename T, int D, int CMAX, bool TMA>
+void launch(const InterpArgs<T>& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
+  GPN_CUDA(
+      cudaFuncSetAttribute(k_interp<T, D, CMAX, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_interp<T, D, CMAX, TMA><<<grid, 256, smem, st>>>(a, tm);
 }
 
-template <typename T, int D>
-void launch_c(const InterpArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+template <typename T, int D, bool TMA>
+void launch_c(const InterpArgs<T>& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
   switch (cmax_bucket(a.cc)) {
-    case 8: launch<T, D, 8>(a, grid, smem, st); break;
-    case 12: launch<T, D, 12>(a, grid, smem, st); break;
-    case 16: launch<T, D, 16>(a, grid, smem, st); break;
-    default: launch<T, D, 32>(a, grid, smem, st);
+    case 8: launch<T, D, 8, TMA>(a, tm, grid, smem, st); break;
+    case 12: launch<T, D, 12, TMA>(a, tm, grid, smem, st); break;
+    case 16: launch<T, D, 16, TMA>(a, tm, grid, smem, st); break;
+    default: launch<T, D, 32, TMA>(a, tm, grid, smem, st);
   }
 }
 
 template <typename T>
 void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, double shift, double* out_sorted, int R,
                  cudaStream_t st) {
+  if (ps.n_active_bins == 0) return;
   const GridGeom& g = plan.geom;
   InterpArgs<T> a{};
   for (int q = 0; q < kMaxDim; ++q) {
@@ -209,8 +242,9 @@ void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, dou
   }
   a.wk = (const T*)ps.wk;
   a.bin_start = ps.bin_start;
+  a.bins = ps.active_bins;
   a.n = ps.n;
-  a.grid = (const T*)plan.grid;
+  a.grid = (const T*)plan.grid_out;
   a.nf = g.nf;
   a.G = plan.grid_elems;
   a.width = g.width;
@@ -218,31 +252,44 @@ void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, dou
   a.inv_halfw = (T)(2.0 / g.width);
   a.tile = g.tile;
   a.ext = g.tile + g.width - 1;
-  a.epitch = g.d == 1 ? a.ext : (a.ext | 1);
+  a.epitch = interp_pitch(g.d, g.tile, g.width, sizeof(T));
   a.C = g.C;
-  size_t per_ch = interp_stage_bytes(g.d, g.tile, g.width, sizeof(T));
-  a.cc = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.C, kInterpSmemBudget / per_ch));
+  a.cc = plan.interp_cc;
+  a.box_bytes = (unsigned)(interp_stage_bytes(g.d, g.tile, g.width, sizeof(T)) * a.cc);
   a.alpha = alpha_sorted;
   a.shift = shift;
   a.out = out_sorted;
-  size_t smem = per_ch * a.cc;
-  dim3 grid((unsigned)ps.nbins_total, (unsigned)R);
+  a.status = plan.dev_status;
+  const size_t smem = 128 + (size_t)a.box_bytes;
+  dim3 grid((unsigned)ps.n_active_bins, (unsigned)R);
   switch (g.d) {
-    case 1: launch_c<T, 1>(a, grid, smem, st); break;
-    case 2: launch_c<T, 2>(a, grid, smem, st); break;
-    default: launch_c<T, 3>(a, grid, smem, st);
+    case 1: launch_c<T, 1, false>(a, plan.tmap_out, grid, smem, st); break;
+    case 2: launch_c<T, 2, true>(a, plan.tmap_out, grid, smem, st); break;
+    default: launch_c<T, 3, true>(a, plan.tmap_out, grid, smem, st);
   }
   GPN_CUDA(cudaGetLastError());
 }
 
 }  // namespace
 
+// Last-dimension pitch of the staged block: for d >= 2 the TMA box width, a
+// multiple of 16 bytes chosen congruent to 4 words mod 8 so that the support rows
+// a lane group reads spread over the banks; for d = 1 the extent itself.
+int interp_pitch(int d, int tile, int width, size_t rs) {
+  int e = tile + width - 1;
+  if (d == 1) return e;
+  const int q = (int)(16 / rs);          // elements per 16 bytes
+  int p = (e + q - 1) / q * q;
+  const int words = (int)(rs / 4);
+  while (((p * words) % 8) != 4) p += q;
+  return p;
+}
+
 size_t interp_stage_bytes(int d, int tile, int width, size_t rs) {
   size_t e = (size_t)tile + width - 1;
   size_t lead = 1;
   for (int q = 0; q < d - 1; ++q) lead *= e;
-  size_t pitch = d == 1 ? e : (e | 1);
-  return lead * pitch * rs;
+  return lead * (size_t)interp_pitch(d, tile, width, rs) * rs;
 }
 
 void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, double shift, double* out_sorted,

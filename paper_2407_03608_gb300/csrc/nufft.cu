@@ -136,9 +136,9 @@ void run_fft_inverse(Plan& plan, int R, cudaStream_t st) {
   cufftHandle h = plan.inv_plan(R);
   GPN_CUFFT(cufftSetStream(h, st));
   if (plan.precision == GP_FP32)
-    GPN_CUFFT(cufftExecC2R(h, (cufftComplex*)plan.spec, (cufftReal*)plan.grid));
+    GPN_CUFFT(cufftExecC2R(h, (cufftComplex*)plan.spec, (cufftReal*)plan.grid_out));
   else
-    GPN_CUFFT(cufftExecZ2D(h, (cufftDoubleComplex*)plan.spec, (cufftDoubleReal*)plan.grid));
+    GPN_CUFFT(cufftExecZ2D(h, (cufftDoubleComplex*)plan.spec, (cufftDoubleReal*)plan.grid_out));
 }
 
 void PhaseProfile::harvest() {

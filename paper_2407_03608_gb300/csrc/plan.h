@@ -4,6 +4,7 @@
 #include <map>
 #include <vector>
 
+#include <cuda.h>
 #include <cufft.h>
 
 #include "common.h"
@@ -24,6 +25,8 @@ struct PointSet {
   void* wk = nullptr;                                  // w_k(x_i) (real_t) [n][C]
   int* perm = nullptr;                                 // sorted position -> caller index
   int* bin_start = nullptr;                            // nbins_total + 1 offsets
+  int* active_bins = nullptr;                          // bins holding at least one point
+  long long n_active_bins = 0;
 };
 
 // Launch parameters shared by the kernels.
@@ -66,7 +69,15 @@ struct Plan {
   // device buffers
   void* a_tensor = nullptr;             // packed A'[p][f] (real_t), p < C(C+1)/2, f over the half box
   long long n_freq = 0;                 // frequencies in the half box
-  void* grid = nullptr;                 // real fine grids, C * max_rhs * nf^d
+  void* grid = nullptr;                 // spreading grids (R2C input), C * max_rhs * nf^d; cells no
+                                        // active tile covers stay zero from plan creation on
+  void* grid_out = nullptr;             // C2R output read by interp, same shape
+  int* active_tiles = nullptr;          // tiles some point's support reaches
+  long long n_active_tiles = 0;
+  int interp_cc = 1;                    // channels per interp staging chunk
+  CUtensorMap tmap_out;                 // TMA descriptor of grid_out (d >= 2)
+  int* dev_status = nullptr;            // set by kernels whose bounded waits ran out
+  int* host_status = nullptr;           // pinned mirror
   void* spec = nullptr;                 // half spectra, C * max_rhs * nf^(d-1) * (nf/2+1) complex
   long long grid_elems = 0, spec_elems = 0;   // per channel
   double* vec_a = nullptr;              // sorted-order work vectors, N * max_rhs each
@@ -97,9 +108,15 @@ struct Plan {
 // l0, bins, permutation, and the Chebyshev weights from the paper-native (w, sigma)
 // fields (device, caller order).  Allocates into ps through plan.alloc.
 // alloc(bytes) returns device memory owned by the caller of build_pointset.
+// The host copy of bin_start is returned in *bin_start_host when not null.
 using DevAlloc = void* (*)(void* ctx, size_t bytes);
 void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double* w_dev, const double* sig_dev,
-                    long long n, cudaStream_t st, DevAlloc alloc, void* alloc_ctx);
+                    long long n, cudaStream_t st, DevAlloc alloc, void* alloc_ctx,
+                    std::vector<int>* bin_start_host = nullptr);
+
+// Read and clear the device status word; fails with GP_ETIMEOUT when a kernel's
+// bounded wait ran out.  Synchronises the stream.
+void check_device_status(Plan& plan, cudaStream_t st);
 
 // Convert (s, l) to (w, sigma) in place (device, n entries), or validate (w, sigma).
 void fields_to_paper(const double* a, const double* b, double* w_out, double* sig_out, long long n, int d, int mode,
@@ -117,6 +134,7 @@ constexpr size_t kInterpSmemBudget = size_t(96) << 10;   // target when sizing c
 constexpr size_t kInterpSmemMax = size_t(200) << 10;      // one staged channel must fit
 int spread_pitch(int d, int tile);
 size_t spread_smem_bytes(int d, int tile, int C, size_t rs);
+int interp_pitch(int d, int tile, int width, size_t rs);
 size_t interp_stage_bytes(int d, int tile, int width, size_t rs);
 
 // Steps (1)+(2a): spread sorted-order coefficients alpha (N x R, float64) onto the

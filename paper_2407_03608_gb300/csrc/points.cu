@@ -235,7 +235,7 @@ void field_stats(const double* x, const double* w, const double* sig, long long 
 }
 
 void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double* w_dev, const double* sig_dev,
-                    long long n, cudaStream_t st, DevAlloc alloc, void* actx) {
+                    long long n, cudaStream_t st, DevAlloc alloc, void* actx, std::vector<int>* bin_start_host) {
   const Hyper& h = plan.h;
   const int d = h.d;
   ps.n = n;
@@ -330,6 +330,17 @@ void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double*
   cudaFree(cub_tmp);
   GPN_CUDA(e);
   GPN_CHECK(hbad == 0, GP_EINVAL, std::to_string(hbad) + " points outside the plan box");
+  // list of non-empty bins (the interp launch set)
+  std::vector<int> hs(ps.nbins_total + 1);
+  GPN_CUDA(cudaMemcpy(hs.data(), ps.bin_start, sizeof(int) * hs.size(), cudaMemcpyDeviceToHost));
+  std::vector<int> act;
+  for (long long b = 0; b < ps.nbins_total; ++b)
+    if (hs[b + 1] > hs[b]) act.push_back((int)b);
+  ps.n_active_bins = (long long)act.size();
+  ps.active_bins = (int*)alloc(actx, sizeof(int) * std::max<size_t>(act.size(), 1));
+  if (!act.empty())
+    GPN_CUDA(cudaMemcpy(ps.active_bins, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice));
+  if (bin_start_host) bin_start_host->swap(hs);
 }
 
 }  // namespace gpn

@@ -5,11 +5,15 @@
 // Output-stationary tiling.  One CTA owns one tile of tile^d fine-grid cells for
 // one right-hand side and accumulates, in shared memory, the contributions of
 // every point whose support meets the tile: with points binned by the first cell
-// of their support, those are the points of the 2^d bins at offsets {0,-1}^d.
-// The work is flattened over (point, pencil) pairs -- a pencil being the `width`
-// cells of a point's support along the last dimension -- so every thread stays
-// busy without warp-level synchronisation.  The tile is then written once with
-// coalesced stores: no global atomics and no pre-zeroing of the grid.
+// of their support, those are the points of the 2^d bins at offsets {0,-1}^d,
+// which form 2^(d-1) contiguous ranges of the sorted points.  The CTA loads the
+// points of each range in batches with coalesced loads into shared memory, then
+// works on (point, pencil) pairs -- a pencil being the `width` cells of a point's
+// support along the last dimension -- so every thread stays busy without warp
+// synchronisation.  The tile is written once with coalesced stores.  Only tiles
+// some point can reach are launched (the plan's active-tile list): the other
+// cells of the spreading grid are zeroed once when the plan is built, and the
+// forward R2C transform leaves its input untouched.  No global atomics.
 // The shared tile's last dimension is padded to an odd pitch so that the rows a
 // warp touches fall in different banks.
 #include "kernels.h"
@@ -18,12 +22,15 @@ namespace gpn {
 
 namespace {
 
+constexpr int kBatch = 256;  // points staged per batch
+
 template <typename T>
 struct SpreadArgs {
   const int* cell0[kMaxDim];
   const T* xi[kMaxDim];
   const T* wk;
   const int* bin_start;
+  const int* tiles;      // active tile ids
   int nbins[kMaxDim];
   const double* alpha;   // sorted order, N x R column-major
   long long n;
@@ -41,19 +48,23 @@ struct SpreadArgs {
 template <typename T, int D, int CMAX>
 __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);
   const int TS = a.tile, TP = a.pitch, W = a.width, C = a.C;
   int lead = 1;  // cells in the leading D-1 dimensions
 #pragma unroll
   for (int q = 0; q < D - 1; ++q) lead *= TS;
   const int TV = lead * TP;  // padded tile volume
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  T* s_xi = tile + (size_t)C * TV;                       // [D][kBatch]
+  T* s_amp = s_xi + D * kBatch;                          // [kBatch]
+  T* s_wk = s_amp + kBatch;                              // [C][kBatch]
+  int* s_l0 = reinterpret_cast<int*>(s_wk + (size_t)C * kBatch);  // [D][kBatch]
   const int r = blockIdx.y;
 
   for (int i = threadIdx.x; i < C * TV; i += blockDim.x) tile[i] = T(0);
 
   int tc[kMaxDim] = {0, 0, 0}, base[kMaxDim] = {0, 0, 0};
   {
-    long long rest = blockIdx.x;
+    long long rest = a.tiles[blockIdx.x];
 #pragma unroll
     for (int q = D - 1; q >= 0; --q) {
       tc[q] = (int)(rest % a.nbins[q]);
@@ -61,7 +72,6 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
       base[q] = tc[q] * TS;
     }
   }
-  __syncthreads();
 
   int P = 1;  // pencils per point
 #pragma unroll
@@ -69,62 +79,79 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   const double* alpha_r = a.alpha + (size_t)r * a.n;
 
 #pragma unroll 1
-  for (int o = 0; o < (1 << D); ++o) {
+  for (int o = 0; o < (1 << (D - 1)); ++o) {
+    // bins (lead - o, last - 1 .. last) are consecutive in the sorted order
     long long lin = 0;
     bool valid = true;
 #pragma unroll
-    for (int q = 0; q < D; ++q) {
+    for (int q = 0; q < D - 1; ++q) {
       int b = tc[q] - ((o >> q) & 1);
       valid = valid && b >= 0;
       lin = lin * a.nbins[q] + (b < 0 ? 0 : b);
     }
     if (!valid) continue;
-    const int p0 = a.bin_start[lin], p1 = a.bin_start[lin + 1];
-    const long long work = (long long)(p1 - p0) * P;
-    for (long long g = threadIdx.x; g < work; g += blockDim.x) {
-      const int pi = (int)(g / P);
-      int pen = (int)(g - (long long)pi * P);
-      const int p = p0 + pi;
-      // leading coordinates of this pencil and their tile-local cells
-      int off = 0;
-      bool inside = true;
-      T plead = T(1);
-      int iq[kMaxDim];
+    const long long lin_hi = lin * a.nbins[D - 1] + tc[D - 1];
+    const long long lin_lo = lin_hi - (tc[D - 1] > 0 ? 1 : 0);
+    const int r0 = a.bin_start[lin_lo], r1 = a.bin_start[lin_hi + 1];
+    for (int b0 = r0; b0 < r1; b0 += kBatch) {
+      const int nb = min(kBatch, r1 - b0);
+      __syncthreads();  // previous batch consumed (and the tile zeroed)
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const int p = b0 + i;
 #pragma unroll
-      for (int q = D - 2; q >= 0; --q) {
-        iq[q] = pen % W;
-        pen /= W;
+        for (int q = 0; q < D; ++q) {
+          s_l0[q * kBatch + i] = a.cell0[q][p];
+          s_xi[q * kBatch + i] = a.xi[q][p];
+        }
+        s_amp[i] = (T)alpha_r[p];
       }
-#pragma unroll
-      for (int q = 0; q < D - 1; ++q) {
-        int c = a.cell0[q][p] + iq[q] - base[q];
-        inside = inside && c >= 0 && c < TS;
-        off = off * TS + c;
+      for (int idx = threadIdx.x; idx < nb * C; idx += blockDim.x) {
+        const int i = idx / C, k = idx - i * C;
+        s_wk[k * kBatch + i] = a.wk[(size_t)b0 * C + idx];
       }
-      const int l0 = a.cell0[D - 1][p];
-      const int lo = max(0, base[D - 1] - l0), hi = min(W, base[D - 1] + TS - l0);
-      if (!inside || lo >= hi) continue;
+      __syncthreads();
+      const int work = nb * P;
+      for (int g = threadIdx.x; g < work; g += blockDim.x) {
+        const int i = g / P;
+        int pen = g - i * P;
+        int off = 0;
+        bool inside = true;
+        int iq[kMaxDim];
 #pragma unroll
-      for (int q = 0; q < D - 1; ++q) plead *= es_psi<T>((T)iq[q] - a.xi[q][p], a.beta, a.inv_halfw);
-      const T amp = plead * (T)alpha_r[p];
-      T s[CMAX];
+        for (int q = D - 2; q >= 0; --q) {
+          iq[q] = pen % W;
+          pen /= W;
+        }
 #pragma unroll
-      for (int k = 0; k < CMAX; ++k) s[k] = k < C ? a.wk[(size_t)p * C + k] * amp : T(0);
-      const T xl = a.xi[D - 1][p];
-      const int row = off * TP + (l0 - base[D - 1]);
-      for (int i = lo; i < hi; ++i) {
-        const T ps = es_psi<T>((T)i - xl, a.beta, a.inv_halfw);
-        T* cellp = tile + row + i;
+        for (int q = 0; q < D - 1; ++q) {
+          const int c = s_l0[q * kBatch + i] + iq[q] - base[q];
+          inside = inside && c >= 0 && c < TS;
+          off = off * TS + c;
+        }
+        const int l0 = s_l0[(D - 1) * kBatch + i];
+        const int lo = max(0, base[D - 1] - l0), hi = min(W, base[D - 1] + TS - l0);
+        if (!inside || lo >= hi) continue;
+        T amp = s_amp[i];
 #pragma unroll
-        for (int k = 0; k < CMAX; ++k)
-          if (k < C) atomicAdd(cellp + (size_t)k * TV, ps * s[k]);
+        for (int q = 0; q < D - 1; ++q) amp *= es_psi<T>((T)iq[q] - s_xi[q * kBatch + i], a.beta, a.inv_halfw);
+        T s[CMAX];
+#pragma unroll
+        for (int k = 0; k < CMAX; ++k) s[k] = k < C ? s_wk[k * kBatch + i] * amp : T(0);
+        const T xl = s_xi[(D - 1) * kBatch + i];
+        T* rowp = tile + off * TP + (l0 - base[D - 1]);
+        for (int c = lo; c < hi; ++c) {
+          const T ps = es_psi<T>((T)c - xl, a.beta, a.inv_halfw);
+#pragma unroll
+          for (int k = 0; k < CMAX; ++k)
+            if (k < C) atomicAdd(rowp + c + (size_t)k * TV, ps * s[k]);
+        }
       }
     }
   }
   __syncthreads();
 
   // write the tile once (cells past nf in a partial last tile are dropped)
-  int vol = lead * TS;
+  const int vol = lead * TS;
   for (int i = threadIdx.x; i < vol; i += blockDim.x) {
     int rem = i;
     long long gidx = 0, gstride = 1;
@@ -132,9 +159,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
     bool in = true;
 #pragma unroll
     for (int q = D - 1; q >= 0; --q) {
-      int c = rem % TS;
+      const int c = rem % TS;
       rem /= TS;
-      long long gq = (long long)base[q] + c;
+      const long long gq = (long long)base[q] + c;
       in = in && gq < a.nf;
       gidx += gq * gstride;
       gstride *= a.nf;
@@ -169,6 +196,7 @@ template <typename T>
 void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
   const GridGeom& g = plan.geom;
   const PointSet& ps = plan.pts;
+  if (plan.n_active_tiles == 0) return;
   SpreadArgs<T> a{};
   for (int q = 0; q < kMaxDim; ++q) {
     a.cell0[q] = ps.cell0[q];
@@ -177,6 +205,7 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
   }
   a.wk = (const T*)ps.wk;
   a.bin_start = ps.bin_start;
+  a.tiles = plan.active_tiles;
   a.alpha = alpha_sorted;
   a.n = ps.n;
   a.grid = (T*)plan.grid;
@@ -189,7 +218,7 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
   a.pitch = spread_pitch(g.d, g.tile);
   a.C = g.C;
   size_t smem = spread_smem_bytes(g.d, g.tile, g.C, sizeof(T));
-  dim3 grid((unsigned)ps.nbins_total, (unsigned)R);
+  dim3 grid((unsigned)plan.n_active_tiles, (unsigned)R);
   switch (g.d) {
     case 1: launch_c<T, 1>(a, grid, smem, st); break;
     case 2: launch_c<T, 2>(a, grid, smem, st); break;
@@ -205,7 +234,9 @@ int spread_pitch(int d, int tile) { return d == 1 ? tile : tile + 1; }
 size_t spread_smem_bytes(int d, int tile, int C, size_t rs) {
   size_t lead = 1;
   for (int q = 0; q < d - 1; ++q) lead *= tile;
-  return lead * spread_pitch(d, tile) * (size_t)C * rs;
+  size_t tilev = lead * spread_pitch(d, tile) * (size_t)C * rs;
+  size_t batch = (size_t)kBatch * ((d + 1 + C) * rs + d * sizeof(int));
+  return tilev + batch;
 }
 
 void launch_spread(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
