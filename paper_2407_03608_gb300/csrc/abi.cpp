@@ -89,7 +89,7 @@ int choose_tile(int d, int C, size_t rs, int width) {
   for (size_t budget : {size_t(64) << 10, size_t(160) << 10}) {
     for (int i = 0; i < nc; ++i) {
       if (c[i] < width - 1) continue;
-      if (spread_smem_bytes(d, c[i], C, rs) <= budget && interp_stage_bytes(d, c[i], width, rs) <= kInterpSmemMax)
+      if (spread_smem_bytes(d, c[i], C, rs, width) <= budget && interp_stage_bytes(d, c[i], width, rs) <= kInterpSmemMax)
         return c[i];
     }
   }

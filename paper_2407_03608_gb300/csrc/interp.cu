@@ -145,16 +145,34 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
 #pragma unroll
       for (int k = 0; k < CMAX; ++k) acc[k] = T(0);
       const int p = p0 + (active ? pi : 0);
-      if (active) {
-        int l0[kMaxDim];
-        T x[kMaxDim];
+      int l0[kMaxDim];
+      T x[kMaxDim];
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
-          l0[q] = a.cell0[q][p] - base[q];
-          x[q] = a.xi[q][p];
+      for (int q = 0; q < D; ++q) {
+        l0[q] = a.cell0[q][p] - base[q];
+        x[q] = a.xi[q][p];
+      }
+      if (D == 1) {
+        if (active) {
+          const T* rowp = st + l0[0];
+          for (int i = 0; i < W; ++i) {
+            const T wgt = es_psi<T>((T)i - x[0], a.beta, a.inv_halfw);
+#pragma unroll
+            for (int k = 0; k < CMAX; ++k)
+              if (k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+          }
         }
-        for (int pen = gl; pen < P; pen += Gs) {
-          int rem = pen, off = 0;
+      } else {
+        // lane j of the group holds psi_q(j - xi_q) for every axis q; the others
+        // fetch them by shuffles (every lane executes every shuffle)
+        const int src = kGroup == 0 ? grp * Gs : 0;
+        T pq[kMaxDim];
+#pragma unroll
+        for (int q = 0; q < D; ++q) pq[q] = gl < W ? es_psi<T>((T)gl - x[q], a.beta, a.inv_halfw) : T(0);
+        for (int pen0 = 0; pen0 < P; pen0 += Gs) {
+          const int pen = pen0 + gl;
+          const bool valid = active && pen < P;
+          int rem = valid ? pen : 0, off = 0;
           T plead = T(1);
           int iq[kMaxDim];
 #pragma unroll
@@ -164,15 +182,17 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
           }
 #pragma unroll
           for (int q = 0; q < D - 1; ++q) {
-            plead *= es_psi<T>((T)iq[q] - x[q], a.beta, a.inv_halfw);
+            plead *= __shfl_sync(0xffffffffu, pq[q], src + iq[q]);
             off = off * E + l0[q] + iq[q];
           }
           const T* rowp = st + (size_t)off * EP + l0[D - 1];
           for (int i = 0; i < W; ++i) {
-            const T wgt = plead * es_psi<T>((T)i - x[D - 1], a.beta, a.inv_halfw);
+            const T wgt = plead * __shfl_sync(0xffffffffu, pq[D - 1], src + i);
+            if (valid) {
 #pragma unroll
-            for (int k = 0; k < CMAX; ++k)
-              if (k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+              for (int k = 0; k < CMAX; ++k)
+                if (k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+            }
           }
         }
       }
@@ -248,7 +268,7 @@ void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, dou
   a.nf = g.nf;
   a.G = plan.grid_elems;
   a.width = g.width;
-  a.beta = (T)g.beta;
+  a.beta = es_beta_arg<T>(g.beta);
   a.inv_halfw = (T)(2.0 / g.width);
   a.tile = g.tile;
   a.ext = g.tile + g.width - 1;

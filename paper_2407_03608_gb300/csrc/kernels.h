@@ -20,11 +20,29 @@ struct Cplx<double> {
 
 // Exponential-of-semicircle spreading kernel psi(s) = exp(beta (sqrt(1 - (2s/w)^2) - 1))
 // for |s| < w/2 (Barnett, Magland & af Klinteberg's ES kernel), s in fine-grid cells.
+// The float version takes beta2 = beta * log2(e) (folded on the host) and uses the
+// hardware base-2 exponential; the double version takes beta itself.
 template <typename T>
-__device__ __forceinline__ T es_psi(T s, T beta, T inv_halfw) {
-  T z = s * inv_halfw;
-  T q = T(1) - z * z;
-  return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
+__device__ __forceinline__ T es_psi(T s, T beta, T inv_halfw);
+
+template <>
+__device__ __forceinline__ float es_psi<float>(float s, float beta2, float inv_halfw) {
+  const float z = s * inv_halfw;
+  const float q = 1.0f - z * z;
+  return q > 0.0f ? exp2f(beta2 * (sqrtf(q) - 1.0f)) : 0.0f;
+}
+
+template <>
+__device__ __forceinline__ double es_psi<double>(double s, double beta, double inv_halfw) {
+  const double z = s * inv_halfw;
+  const double q = 1.0 - z * z;
+  return q > 0.0 ? exp(beta * (sqrt(q) - 1.0)) : 0.0;
+}
+
+// Kernel shape parameter as the device code expects it (see es_psi).
+template <typename T>
+inline T es_beta_arg(double beta) {
+  return sizeof(T) == 4 ? (T)(beta * 1.4426950408889634074) : (T)beta;
 }
 
 // Channel-count buckets: kernels keep per-channel values in registers sized by a

@@ -247,6 +247,10 @@ bool fft_friendly(long long n) {
   return n == 1 || n == 3;
 }
 
+// Spreading width for a NUFFT tolerance at upsampling sigma: the ES kernel's
+// error behaves like c exp(-pi w sqrt(1 - 1/sigma)) with c between 3 and 6 for
+// sigma in [1.25, 2] (checked against brute-force NUDFTs), so w is the smallest
+// width with 6 exp(-pi w sqrt(1 - 1/sigma)) <= tol.
 int width_for(double tol, double sigma) {
   double w = std::log(6.0 / tol) / (kPi * std::sqrt(1.0 - 1.0 / sigma));
   return std::max(2, (int)std::ceil(w - 1e-9));

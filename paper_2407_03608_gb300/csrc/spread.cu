@@ -6,11 +6,13 @@
 // one right-hand side and accumulates, in shared memory, the contributions of
 // every point whose support meets the tile: with points binned by the first cell
 // of their support, those are the points of the 2^d bins at offsets {0,-1}^d,
-// which form 2^(d-1) contiguous ranges of the sorted points.  The CTA loads the
-// points of each range in batches with coalesced loads into shared memory, then
-// works on (point, pencil) pairs -- a pencil being the `width` cells of a point's
-// support along the last dimension -- so every thread stays busy without warp
-// synchronisation.  The tile is written once with coalesced stores.  Only tiles
+// which form 2^(d-1) contiguous ranges of the sorted points.  For each batch of
+// candidates the CTA keeps the points whose support actually meets the tile
+// (compacted through a shared counter) and tabulates their kernel values per axis
+// in shared memory; then a group of lanes works on each point: in 2-D one lane per
+// support row (a "pencil" of `width` cells along the last axis), in 3-D the warp's
+// lanes over the width^2 pencils, in 1-D one lane per point.  The tile is written
+// once with coalesced stores.  Only tiles
 // some point can reach are launched (the plan's active-tile list): the other
 // cells of the spreading grid are zeroed once when the plan is built, and the
 // forward R2C transform leaves its input untouched.  No global atomics.
@@ -22,7 +24,7 @@ namespace gpn {
 
 namespace {
 
-constexpr int kBatch = 256;  // points staged per batch
+constexpr int kBatch = 128;  // points staged per batch
 
 template <typename T>
 struct SpreadArgs {
@@ -48,16 +50,19 @@ struct SpreadArgs {
 template <typename T, int D, int CMAX>
 __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_count;
   const int TS = a.tile, TP = a.pitch, W = a.width, C = a.C;
   int lead = 1;  // cells in the leading D-1 dimensions
 #pragma unroll
   for (int q = 0; q < D - 1; ++q) lead *= TS;
   const int TV = lead * TP;  // padded tile volume
+  const int PSTR = (D * W) | 1;  // odd stride of a point's kernel-value table
   T* tile = reinterpret_cast<T*>(smem_raw);
-  T* s_xi = tile + (size_t)C * TV;                       // [D][kBatch]
-  T* s_amp = s_xi + D * kBatch;                          // [kBatch]
+  T* s_psi = tile + (size_t)C * TV;                      // [kBatch][PSTR]: psi_q(j - xi_q), q-major
+  T* s_amp = s_psi + (size_t)kBatch * PSTR;              // [kBatch] alpha of the point
   T* s_wk = s_amp + kBatch;                              // [C][kBatch]
   int* s_l0 = reinterpret_cast<int*>(s_wk + (size_t)C * kBatch);  // [D][kBatch]
+  int* s_pid = s_l0 + D * kBatch;                        // [kBatch] sorted point index
   const int r = blockIdx.y;
 
   for (int i = threadIdx.x; i < C * TV; i += blockDim.x) tile[i] = T(0);
@@ -72,7 +77,13 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
       base[q] = tc[q] * TS;
     }
   }
-
+  // lane groups: one point per group; in 2-D a lane is a support row, in 3-D the
+  // warp's lanes run over the width^2 pencils, in 1-D a lane is a whole point
+  constexpr int kGroup = D == 1 ? 1 : (D == 2 ? 0 : 32);
+  const int Gs = kGroup == 0 ? W : kGroup;
+  const int ppw = 32 / Gs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int grp = lane / Gs, gl = lane - grp * Gs;
   int P = 1;  // pencils per point
 #pragma unroll
   for (int q = 0; q < D - 1; ++q) P *= W;
@@ -96,54 +107,77 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
     for (int b0 = r0; b0 < r1; b0 += kBatch) {
       const int nb = min(kBatch, r1 - b0);
       __syncthreads();  // previous batch consumed (and the tile zeroed)
+      if (threadIdx.x == 0) s_count = 0;
+      __syncthreads();
+      // keep only the candidates whose support meets this tile
       for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const int p = b0 + i;
+        int l0[kMaxDim];
+        bool meets = true;
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-          s_l0[q * kBatch + i] = a.cell0[q][p];
-          s_xi[q * kBatch + i] = a.xi[q][p];
+          l0[q] = a.cell0[q][p];
+          meets = meets && l0[q] + W > base[q] && l0[q] < base[q] + TS;
         }
-        s_amp[i] = (T)alpha_r[p];
-      }
-      for (int idx = threadIdx.x; idx < nb * C; idx += blockDim.x) {
-        const int i = idx / C, k = idx - i * C;
-        s_wk[k * kBatch + i] = a.wk[(size_t)b0 * C + idx];
+        if (meets) {
+          const int slot = atomicAdd(&s_count, 1);
+#pragma unroll
+          for (int q = 0; q < D; ++q) s_l0[q * kBatch + slot] = l0[q];
+          s_pid[slot] = p;
+          s_amp[slot] = (T)alpha_r[p];
+        }
       }
       __syncthreads();
-      const int work = nb * P;
-      for (int g = threadIdx.x; g < work; g += blockDim.x) {
-        const int i = g / P;
-        int pen = g - i * P;
-        int off = 0;
-        bool inside = true;
-        int iq[kMaxDim];
+      const int nrel = s_count;
+      for (int slot = threadIdx.x; slot < nrel; slot += blockDim.x) {
+        const int p = s_pid[slot];
+        const T* wkp = a.wk + (size_t)p * C;
 #pragma unroll
-        for (int q = D - 2; q >= 0; --q) {
-          iq[q] = pen % W;
-          pen /= W;
-        }
+        for (int k = 0; k < CMAX; ++k)
+          if (k < C) s_wk[k * kBatch + slot] = wkp[k];
+        T* psi = s_psi + slot * PSTR;
 #pragma unroll
-        for (int q = 0; q < D - 1; ++q) {
-          const int c = s_l0[q * kBatch + i] + iq[q] - base[q];
-          inside = inside && c >= 0 && c < TS;
-          off = off * TS + c;
+        for (int q = 0; q < D; ++q) {
+          const T xq = a.xi[q][p];
+          for (int j = 0; j < W; ++j) psi[q * W + j] = es_psi<T>((T)j - xq, a.beta, a.inv_halfw);
         }
+      }
+      __syncthreads();
+      for (int pb = warp * ppw; pb < nrel; pb += nwarps * ppw) {
+        const int i = pb + grp;
+        if (grp >= ppw || i >= nrel) continue;
+        const T* psi = s_psi + i * PSTR;
         const int l0 = s_l0[(D - 1) * kBatch + i];
         const int lo = max(0, base[D - 1] - l0), hi = min(W, base[D - 1] + TS - l0);
-        if (!inside || lo >= hi) continue;
-        T amp = s_amp[i];
+        T wk[CMAX];
 #pragma unroll
-        for (int q = 0; q < D - 1; ++q) amp *= es_psi<T>((T)iq[q] - s_xi[q * kBatch + i], a.beta, a.inv_halfw);
-        T s[CMAX];
+        for (int k = 0; k < CMAX; ++k) wk[k] = k < C ? s_wk[k * kBatch + i] * s_amp[i] : T(0);
+        for (int pen = gl; pen < P; pen += Gs) {
+          int rem = pen, off = 0;
+          bool inside = true;
+          T amp = T(1);
+          int iq[kMaxDim];
 #pragma unroll
-        for (int k = 0; k < CMAX; ++k) s[k] = k < C ? s_wk[k * kBatch + i] * amp : T(0);
-        const T xl = s_xi[(D - 1) * kBatch + i];
-        T* rowp = tile + off * TP + (l0 - base[D - 1]);
-        for (int c = lo; c < hi; ++c) {
-          const T ps = es_psi<T>((T)c - xl, a.beta, a.inv_halfw);
+          for (int q = D - 2; q >= 0; --q) {
+            iq[q] = rem % W;
+            rem /= W;
+          }
 #pragma unroll
-          for (int k = 0; k < CMAX; ++k)
-            if (k < C) atomicAdd(rowp + c + (size_t)k * TV, ps * s[k]);
+          for (int q = 0; q < D - 1; ++q) {
+            const int c = s_l0[q * kBatch + i] + iq[q] - base[q];
+            inside = inside && c >= 0 && c < TS;
+            off = off * TS + c;
+            amp *= psi[q * W + iq[q]];
+          }
+          if (!inside) continue;
+          const T* plast = psi + (D - 1) * W;
+          T* rowp = tile + off * TP + (l0 - base[D - 1]);
+          for (int c = lo; c < hi; ++c) {
+            const T ps = amp * plast[c];
+#pragma unroll
+            for (int k = 0; k < CMAX; ++k)
+              if (k < C) atomicAdd(rowp + c + (size_t)k * TV, ps * wk[k]);
+          }
         }
       }
     }
@@ -212,12 +246,12 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
   a.nf = g.nf;
   a.G = plan.grid_elems;
   a.width = g.width;
-  a.beta = (T)g.beta;
+  a.beta = es_beta_arg<T>(g.beta);
   a.inv_halfw = (T)(2.0 / g.width);
   a.tile = g.tile;
   a.pitch = spread_pitch(g.d, g.tile);
   a.C = g.C;
-  size_t smem = spread_smem_bytes(g.d, g.tile, g.C, sizeof(T));
+  size_t smem = spread_smem_bytes(g.d, g.tile, g.C, sizeof(T), g.width);
   dim3 grid((unsigned)plan.n_active_tiles, (unsigned)R);
   switch (g.d) {
     case 1: launch_c<T, 1>(a, grid, smem, st); break;
@@ -231,11 +265,11 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
 
 int spread_pitch(int d, int tile) { return d == 1 ? tile : tile + 1; }
 
-size_t spread_smem_bytes(int d, int tile, int C, size_t rs) {
+size_t spread_smem_bytes(int d, int tile, int C, size_t rs, int width) {
   size_t lead = 1;
   for (int q = 0; q < d - 1; ++q) lead *= tile;
   size_t tilev = lead * spread_pitch(d, tile) * (size_t)C * rs;
-  size_t batch = (size_t)kBatch * ((d + 1 + C) * rs + d * sizeof(int));
+  size_t batch = (size_t)kBatch * ((((size_t)d * width) | 1) * rs + (1 + C) * rs + (d + 1) * sizeof(int));
   return tilev + batch;
 }
 

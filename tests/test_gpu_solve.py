@@ -76,7 +76,7 @@ def test_multi_rhs_solve_equals_single(gpn):
 
 
 def test_refined_mixed_precision_solve(gpn):
-    w = gpinputs.config_2d(4000, 1.5)
+    w = gpinputs.config_1d(2000)
     hi = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-6, precision=gpn.GP_FP64)
     lo = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-6, precision=gpn.GP_FP32, **hi.matched_opts())
     y = torch.from_numpy(w.y).cuda()
