@@ -44,8 +44,8 @@ class gp_plan_opts(ctypes.Structure):
                 ("M", ctypes.c_longlong), ("dw", ctypes.c_double),
                 ("nufft_tol", ctypes.c_double), ("upsampfac", ctypes.c_double),
                 ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
-                ("nf", ctypes.c_longlong), ("tile", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("max_bytes", ctypes.c_longlong)]
+                ("nf", ctypes.c_longlong), ("tile", ctypes.c_int), ("transform", ctypes.c_int),
+                ("max_rhs", ctypes.c_int), ("max_bytes", ctypes.c_longlong)]
 
 
 class gp_plan_info(ctypes.Structure):
@@ -56,6 +56,7 @@ class gp_plan_info(ctypes.Structure):
                 ("M", ctypes.c_longlong), ("dw", ctypes.c_double), ("nf", ctypes.c_longlong),
                 ("kernel_width", ctypes.c_int), ("kernel_beta", ctypes.c_double),
                 ("upsampfac", ctypes.c_double), ("nufft_tol", ctypes.c_double), ("tile", ctypes.c_int),
+                ("transform", ctypes.c_int),
                 ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
                 ("est_err_t", ctypes.c_double), ("est_err_sigma", ctypes.c_double),
                 ("est_err_trunc", ctypes.c_double), ("est_err_alias", ctypes.c_double),

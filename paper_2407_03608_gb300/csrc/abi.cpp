@@ -135,6 +135,7 @@ Plan::~Plan() {
   prof.destroy();
   for (auto& kv : fft_fwd) cufftDestroy(kv.second);
   for (auto& kv : fft_inv) cufftDestroy(kv.second);
+  for (auto& kv : fft_col) cufftDestroy(kv.second);
   for (void* p : owned) cudaFree(p);
   if (host_scal) cudaFreeHost(host_scal);
   if (host_status) cudaFreeHost(host_status);
@@ -196,6 +197,32 @@ void build_active_tiles(Plan& plan, const std::vector<int>& bstart) {
   plan.active_tiles = (int*)plan.alloc(sizeof(int) * std::max<size_t>(act.size(), 1));
   if (!act.empty())
     GPN_CUDA(cudaMemcpy(plan.active_tiles, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice));
+}
+
+// Rows (first axis) and columns (last axis) of the fine grid that hold spread data
+// or that the interpolation reads: the active tiles' extent plus one kernel width.
+void set_data_extent(Plan& plan) {
+  const int d = plan.h.d, TS = plan.h.tile;
+  const long long nf = plan.h.nf;
+  std::vector<int> t(plan.n_active_tiles);
+  if (plan.n_active_tiles)
+    GPN_CUDA(cudaMemcpy(t.data(), plan.active_tiles, sizeof(int) * t.size(), cudaMemcpyDeviceToHost));
+  long long lo[kMaxDim] = {nf, nf, nf}, hi[kMaxDim] = {0, 0, 0};
+  for (int id : t) {
+    long long rest = id;
+    for (int q = d - 1; q >= 0; --q) {
+      long long c = rest % plan.pts.nbins[q];
+      rest /= plan.pts.nbins[q];
+      lo[q] = std::min(lo[q], c * TS);
+      hi[q] = std::max(hi[q], std::min(nf, (c + 1) * TS + plan.h.width));
+    }
+  }
+  if (t.empty())
+    for (int q = 0; q < d; ++q) lo[q] = hi[q] = 0;
+  plan.col_lo = (int)lo[d - 1];
+  plan.col_hi = (int)hi[d - 1];
+  plan.row_lo = d == 2 ? (int)lo[0] : 0;
+  plan.row_hi = d == 2 ? (int)hi[0] : 1;
 }
 
 // TMA descriptor of the interp input grid: dims (nf, ..., nf, C * max_rhs), box =
@@ -324,7 +351,7 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->grid_elems = G;
   plan->spec_elems = S;
   plan->n_freq = nfreq;
-  long long est = (long long)(C * (long long)max_rhs * (2 * G * rs + S * 2 * rs)) * 2  // grids + cuFFT work
+  long long est = (long long)(C * (long long)max_rhs * (2 * G * rs + S * 2 * rs)) * 2  // grids + transforms
                   + (long long)(C * (C + 1) / 2) * nfreq * (long long)rs + N * (long long)(d * (4 + rs) + 4 + C * rs) +
                   (long long)N * max_rhs * 8 * 9;
   GPN_CHECK(o.max_bytes <= 0 || est <= o.max_bytes, GP_ENOMEM,
@@ -338,7 +365,26 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->grid = plan->alloc((size_t)C * max_rhs * G * rs);
   GPN_CUDA(cudaMemsetAsync(plan->grid, 0, (size_t)C * max_rhs * G * rs, st));
   plan->grid_out = plan->alloc((size_t)C * max_rhs * G * rs);
-  plan->spec = plan->alloc((size_t)C * max_rhs * S * 2 * rs);
+  GPN_CUDA(cudaMemsetAsync(plan->grid_out, 0, (size_t)C * max_rhs * G * rs, st));
+  GPN_CHECK(o.transform >= 0 && o.transform <= 2, GP_EINVAL, "transform must be 0, 1 or 2");
+  const bool row_ok = rowfft_supported(d, h.nf, rs);
+  GPN_CHECK(o.transform != 2 || row_ok, GP_EUNSUPPORTED, "pruned row transforms need d <= 2 and power-of-two nf");
+  // auto: the pruned transforms remove FP64 FFT arithmetic (ALU-bound on GB300);
+  // in FP32 the full-grid cuFFT plans are currently the faster choice
+  plan->rowfft = o.transform == 2 || (o.transform == 0 && row_ok && o.precision == GP_FP64);
+  if (plan->rowfft) {
+    set_data_extent(*plan);
+    const size_t rows = d == 2 ? (size_t)h.nf : 1;
+    const size_t fbytes = rows * C * (size_t)max_rhs * (h.M + 1) * 2 * rs;
+    plan->fx = plan->alloc(fbytes);
+    plan->fy = plan->alloc(fbytes);
+    plan->fz = plan->alloc(fbytes);
+    GPN_CUDA(cudaMemsetAsync(plan->fx, 0, fbytes, st));
+    GPN_CUDA(cudaMemsetAsync(plan->fz, 0, fbytes, st));
+    build_twiddles(*plan);
+  } else {
+    plan->spec = plan->alloc((size_t)C * max_rhs * S * 2 * rs);
+  }
   plan->interp_cc = (int)std::max<size_t>(
       1, std::min<size_t>((size_t)C, kInterpSmemBudget / interp_stage_bytes(d, h.tile, h.width, rs)));
   if (d >= 2) make_tensor_map(*plan);
@@ -358,8 +404,12 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->scal = (double*)plan->alloc(sizeof(double) * 8 * max_rhs);
   plan->partials = (double*)plan->alloc(sizeof(double) * 512 * max_rhs);
   GPN_CUDA(cudaMallocHost(&plan->host_scal, sizeof(double) * 8 * max_rhs));
-  plan->fwd_plan(1);
-  plan->inv_plan(1);
+  if (plan->rowfft) {
+    if (d == 2) plan->col_plan(1);
+  } else {
+    plan->fwd_plan(1);
+    plan->inv_plan(1);
+  }
   GPN_CUDA(cudaStreamSynchronize(st));
   GPN_CHECK(plan->max_bytes <= 0 || plan->bytes <= plan->max_bytes, GP_ENOMEM, "plan exceeds max_bytes");
   return plan.release();
@@ -591,6 +641,7 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->upsampfac = h.upsamp;
     info->nufft_tol = h.nufft_tol;
     info->tile = h.tile;
+    info->transform = p->rowfft ? 2 : 1;
     for (int q = 0; q < 3; ++q) {
       info->box_lo[q] = h.box_lo[q];
       info->box_hi[q] = h.box_hi[q];

@@ -124,6 +124,7 @@ cufftHandle Plan::inv_plan(int R) {
 }
 
 void run_fft_forward(Plan& plan, int R, cudaStream_t st) {
+  if (plan.rowfft) return rowfft_forward(plan, R, st);
   cufftHandle h = plan.fwd_plan(R);
   GPN_CUFFT(cufftSetStream(h, st));
   if (plan.precision == GP_FP32)
@@ -133,6 +134,7 @@ void run_fft_forward(Plan& plan, int R, cudaStream_t st) {
 }
 
 void run_fft_inverse(Plan& plan, int R, cudaStream_t st) {
+  if (plan.rowfft) return rowfft_inverse(plan, R, st);
   cufftHandle h = plan.inv_plan(R);
   GPN_CUFFT(cufftSetStream(h, st));
   if (plan.precision == GP_FP32)

@@ -242,9 +242,11 @@ double inv_gamma_q(double a, double target) {
   return std::exp(0.5 * (lo + hi));
 }
 
-bool fft_friendly(long long n) {
+// Fine-grid sizes: powers of two (the pruned row transforms of d <= 2 need them,
+// and cuFFT is fastest there), and also 3 * 2^a in 3-D.
+bool fft_friendly(long long n, int d) {
   while (n % 2 == 0) n /= 2;
-  return n == 1 || n == 3;
+  return n == 1 || (d == 3 && n == 3);
 }
 
 // Spreading width for a NUFFT tolerance at upsampling sigma: the ES kernel's
@@ -393,7 +395,7 @@ void select_hyper(Hyper& h, const gp_plan_opts& o, int precision, long long /*n_
     GPN_CHECK(nf > modes, GP_EINVAL, "nf must exceed 2M+1");
   } else {
     nf = 16;
-    while (nf < (long long)std::ceil(min_up * modes) || !fft_friendly(nf)) ++nf;
+    while (nf < (long long)std::ceil(min_up * modes) || !fft_friendly(nf, d)) ++nf;
   }
   for (;;) {
     h.nf = nf;
@@ -404,7 +406,7 @@ void select_hyper(Hyper& h, const gp_plan_opts& o, int precision, long long /*n_
     bool fits = h.width <= kMaxWidth && occ <= nf;
     if (fits || (o.set & GP_SET_NF)) break;
     ++nf;
-    while (!fft_friendly(nf)) ++nf;
+    while (!fft_friendly(nf, d)) ++nf;
   }
   GPN_CHECK(h.width <= kMaxWidth, GP_EINVAL, "spreading kernel wider than 16 cells: raise nf or nufft_tol");
   GPN_CHECK(L / P * h.nf + h.width + 4 <= h.nf, GP_EINVAL, "points do not fit in the fine grid without wrap-around");

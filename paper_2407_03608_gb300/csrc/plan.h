@@ -92,7 +92,20 @@ struct Plan {
   double* host_scal = nullptr;          // pinned mirror
   double* stage_in = nullptr;           // staging for host-pointer calls, N * max_rhs
   double* stage_out = nullptr;
-  std::map<int, cufftHandle> fft_fwd, fft_inv;  // keyed by R
+  std::map<int, cufftHandle> fft_fwd, fft_inv;  // keyed by R (full-grid path)
+  // pruned transform path (d <= 2, power-of-two nf): compact spectra
+  // [rows][C*R][M+1] and the data extent of the fine grid
+  bool rowfft = false;
+  void* fx = nullptr;                   // row-transform output (rows without data stay zero)
+  void* fy = nullptr;                   // column-transform output / inverse-column output
+  void* fz = nullptr;                   // step-3 output (rows |m0| > M stay zero)
+  void* twiddle = nullptr;              // exp(-2 pi i k / nf), k < nf
+  void* stage_twiddle = nullptr;        // per-stage twiddles of the length-nf/2 FFT
+  int fft_log2h = 0;                    // log2(nf / 2)
+  int row_lo = 0, row_hi = 0;           // grid rows holding data (first axis, d = 2)
+  int col_lo = 0, col_hi = 0;           // grid columns holding data or read by interp (last axis)
+  std::map<int, cufftHandle> fft_col;   // first-axis C2C plans keyed by R
+  cufftHandle col_plan(int R);
   long long bytes = 0;
   std::vector<void*> owned;             // every cudaMalloc of the plan
 
@@ -149,6 +162,13 @@ void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, d
 // FFTs of the fine grids (forward R2C, inverse C2R), batched over C * R.
 void run_fft_forward(Plan& plan, int R, cudaStream_t st);
 void run_fft_inverse(Plan& plan, int R, cudaStream_t st);
+
+// Pruned transforms (fft_rows.cu).
+bool rowfft_supported(int d, long long nf, size_t rs);
+void build_twiddles(Plan& plan);
+void rowfft_forward(Plan& plan, int R, cudaStream_t st);
+void rowfft_diag(Plan& plan, int R, cudaStream_t st);
+void rowfft_inverse(Plan& plan, int R, cudaStream_t st);
 
 // Full matvec in sorted order: out = (K~ + shift I) alpha.
 void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st);

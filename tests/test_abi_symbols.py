@@ -68,8 +68,8 @@ def test_struct_layout_matches_header(lib, tmp_path):
 int main(void) {
   printf("gp_plan_opts %zu\n", sizeof(gp_plan_opts));
   printf("gp_plan_info %zu\n", sizeof(gp_plan_info));
-  F(gp_plan_opts, set) F(gp_plan_opts, M) F(gp_plan_opts, box_lo) F(gp_plan_opts, nf) F(gp_plan_opts, max_bytes)
-  F(gp_plan_info, M) F(gp_plan_info, nf) F(gp_plan_info, box_hi) F(gp_plan_info, est_err_alias)
+  F(gp_plan_opts, set) F(gp_plan_opts, M) F(gp_plan_opts, box_lo) F(gp_plan_opts, nf) F(gp_plan_opts, transform) F(gp_plan_opts, max_bytes)
+  F(gp_plan_info, M) F(gp_plan_info, nf) F(gp_plan_info, transform) F(gp_plan_info, box_hi) F(gp_plan_info, est_err_alias)
   F(gp_plan_info, bytes_resident) F(gp_plan_info, max_rhs)
   return 0;
 }

@@ -64,14 +64,20 @@ CASES = [
 
 @pytest.mark.parametrize("d,n,nu,n_t,n_sigma,M", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_matvec_vs_exact_nudft(gpn, d, n, nu, n_t, n_sigma, M, precision):
+@pytest.mark.parametrize("transform", [1, 2])
+def test_matvec_vs_exact_nudft(gpn, d, n, nu, n_t, n_sigma, M, precision, transform):
+    """transform 1: full-grid cuFFT R2C/C2R; 2: pruned row transforms (d <= 2)."""
+    if transform == 2 and d == 3:
+        pytest.skip("pruned row transforms cover d <= 2")
     w = small_case(d, n, 0)
     X = w.points
     wp, sig = okern.paper_fields(w.s, w.l, d)
     p = explicit_params(d, nu, sig, X, n_t=n_t, n_sigma=n_sigma, M=M)
     prec = gpn.GP_FP64 if precision == "fp64" else gpn.GP_FP32
     tol = 1e-11 if precision == "fp64" else 1e-6
-    plan = gpn.Plan(X, w.s, w.l, nu=nu, eps=1e-6, precision=prec, nufft_tol=tol, **plan_kwargs(p))
+    plan = gpn.Plan(X, w.s, w.l, nu=nu, eps=1e-6, precision=prec, nufft_tol=tol, transform=transform,
+                    **plan_kwargs(p))
+    assert plan.info["transform"] == transform
     alpha = gpinputs.random_alpha(n, 1, seed=11)
     ref = ktilde.matvec(X, wp, sig, alpha, p)
     got = plan.matvec(torch.from_numpy(alpha).cuda()).cpu().numpy()
@@ -88,14 +94,27 @@ def test_matvec_host_pointers_match_device(gpn):
     assert rel(host, dev) < 1e-14
 
 
-def test_matvec_multi_rhs_equals_columns(gpn):
+@pytest.mark.parametrize("transform", [1, 2])
+def test_matvec_multi_rhs_equals_columns(gpn, transform):
     w = gpinputs.config_2d(800, 1.5)
-    plan = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-4, max_rhs=3)
+    plan = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-4, max_rhs=3, transform=transform)
     A = gpinputs.random_alpha(800, 3, seed=4)
     full = plan.matvec(torch.from_numpy(A).cuda()).cpu().numpy()
     for r in range(3):
         col = plan.matvec(torch.from_numpy(A[:, r].copy()).cuda()).cpu().numpy()
         assert rel(full[:, r], col) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pruned_transforms_match_full_grid(gpn, precision):
+    """The pruned row/column transforms compute the same K~ alpha as the full 2-D cuFFT path."""
+    w = gpinputs.config_2d(3000, 1.5)
+    prec = gpn.GP_FP64 if precision == "fp64" else gpn.GP_FP32
+    full = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-5, precision=prec, transform=1)
+    pruned = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-5, precision=prec, transform=2, **full.matched_opts())
+    a = torch.from_numpy(w.alpha).cuda()
+    e = rel(pruned.matvec(a).cpu().numpy(), full.matvec(a).cpu().numpy())
+    assert e <= (1e-12 if precision == "fp64" else 2e-6), e
 
 
 def test_shift_adds_eta2_alpha(gpn):
