@@ -23,6 +23,7 @@ struct PointSet {
   int* cell0[kMaxDim] = {nullptr, nullptr, nullptr};   // l0_a, sorted order
   void* xi[kMaxDim] = {nullptr, nullptr, nullptr};     // xi_a (real_t), sorted order
   void* wk = nullptr;                                  // w_k(x_i) (real_t) [n][C]
+  float* wabs = nullptr;                               // max_k |w_k(x_i)| [n]
   int* perm = nullptr;                                 // sorted position -> caller index
   int* bin_start = nullptr;                            // nbins_total + 1 offsets
   int* active_bins = nullptr;                          // bins holding at least one point

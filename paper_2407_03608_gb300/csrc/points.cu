@@ -141,7 +141,7 @@ template <typename T>
 __global__ void k_gather_points(const int* __restrict__ perm, long long n, int d, const int* __restrict__ l0_in,
                                 const double* __restrict__ xi_in, int* c0, int* c1, int* c2, T* x0, T* x1, T* x2,
                                 const double* __restrict__ w, const double* __restrict__ sig, ChebArgs cb,
-                                T* __restrict__ wk) {
+                                T* __restrict__ wk, float* __restrict__ wabs) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= n) return;
   long long i = perm[p];
@@ -160,11 +160,18 @@ __global__ void k_gather_points(const int* __restrict__ perm, long long n, int d
     if (s == cb.nodes[k]) hit = k;
   if (hit >= 0 || cb.C == 1) {
     for (int k = 0; k < cb.C; ++k) wk[p * cb.C + k] = (T)((k == hit || cb.C == 1) ? pre : 0.0);
+    wabs[p] = (float)fabs(pre);
     return;
   }
   double den = 0.0;
   for (int k = 0; k < cb.C; ++k) den += cb.bary[k] / (s - cb.nodes[k]);
-  for (int k = 0; k < cb.C; ++k) wk[p * cb.C + k] = (T)(pre * (cb.bary[k] / (s - cb.nodes[k])) / den);
+  double m = 0.0;
+  for (int k = 0; k < cb.C; ++k) {
+    const double v = pre * (cb.bary[k] / (s - cb.nodes[k])) / den;
+    wk[p * cb.C + k] = (T)v;
+    m = fmax(m, fabs(v));
+  }
+  wabs[p] = (float)m;
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -284,6 +291,7 @@ void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double*
   }
   ps.perm = (int*)alloc(actx, sizeof(int) * nn);
   ps.wk = alloc(actx, rs * nn * plan.geom.C);
+  ps.wabs = (float*)alloc(actx, sizeof(float) * nn);
   ps.bin_start = (int*)alloc(actx, sizeof(int) * (ps.nbins_total + 1));
   unsigned long long hbad = 0;
   if (e == cudaSuccess) {
@@ -311,11 +319,11 @@ void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double*
       if (plan.precision == GP_FP32)
         k_gather_points<float><<<blocks_for(n, 256), 256, 0, st>>>(
             ps.perm, n, d, l0_tmp, xi_tmp, ps.cell0[0], ps.cell0[1], ps.cell0[2], (float*)ps.xi[0], (float*)ps.xi[1],
-            (float*)ps.xi[2], w_dev, sig_dev, cb, (float*)ps.wk);
+            (float*)ps.xi[2], w_dev, sig_dev, cb, (float*)ps.wk, ps.wabs);
       else
         k_gather_points<double><<<blocks_for(n, 256), 256, 0, st>>>(
             ps.perm, n, d, l0_tmp, xi_tmp, ps.cell0[0], ps.cell0[1], ps.cell0[2], (double*)ps.xi[0],
-            (double*)ps.xi[1], (double*)ps.xi[2], w_dev, sig_dev, cb, (double*)ps.wk);
+            (double*)ps.xi[1], (double*)ps.xi[2], w_dev, sig_dev, cb, (double*)ps.wk, ps.wabs);
     }
     chk(cudaGetLastError());
     chk(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st));

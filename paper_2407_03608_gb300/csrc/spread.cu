@@ -15,7 +15,8 @@
 // once with coalesced stores.  Only tiles
 // some point can reach are launched (the plan's active-tile list): the other
 // cells of the spreading grid are zeroed once when the plan is built, and the
-// forward R2C transform leaves its input untouched.  No global atomics.
+// forward R2C transform leaves its input untouched.  No global atomics; the
+// shared tile of the FP32 path accumulates in int32 fixed point (see SpreadAcc).
 // The shared tile's last dimension is padded to an odd pitch so that the rows a
 // warp touches fall in different banks.
 #include "kernels.h"
@@ -31,6 +32,7 @@ struct SpreadArgs {
   const int* cell0[kMaxDim];
   const T* xi[kMaxDim];
   const T* wk;
+  const float* wabs;     // max_k |w_k(x_i)|
   const int* bin_start;
   const int* tiles;      // active tile ids
   int nbins[kMaxDim];
@@ -45,27 +47,56 @@ struct SpreadArgs {
   int tile;
   int pitch;             // padded extent of the last tile dimension in shared memory
   int C;
+  unsigned pmagic;       // ceil(2^24 / P): (g * pmagic) >> 24 == g / P for g < 2^24 / P
+  unsigned wmagic;       // ceil(2^12 / width): (x * wmagic) >> 12 == x / width for x < 256
+};
+
+// Accumulator of the shared tile.  Float atomics on shared memory are emulated on
+// sm_103 (compare-and-swap; measured 2.9 T/s and slowing with every address
+// collision), and so are 64-bit integer atomics, while 32-bit integer atomics are
+// native (8.2 T/s, collisions combined in hardware).  The FP32 path therefore
+// accumulates in fixed point held as two int32 words per cell.  Each contribution
+// v, already scaled by 2^e, is split with float arithmetic only:
+//   hi = floor(v / 2^16)          (|hi| < 2^22, so hi is exact as a float)
+//   lo = round(v - hi * 2^16)     (one FMA, exact; 0 <= lo <= 2^16)
+// both converted to int32 by adding 1.5 * 2^23, which leaves round(x) in the low
+// mantissa bits for |x| < 2^22, and the cell is sum(hi) * 2^16 + sum(lo).  e is
+// chosen per tile so that S 2^e <= 2^38 with S = sum over the points reaching the
+// tile of max_k |w_k| |alpha| (a bound on every cell since psi <= 1); the hi sums
+// stay inside int32 and the lo sums below 2^31 for up to 32768 contributions per
+// cell.  The resolution is S 2^-38, far below the float rounding of the products.  The FP64 path
+// keeps float64 atomics (it is bound by its FFTs).
+template <typename T>
+struct SpreadAcc {
+  using type = T;
+};
+template <>
+struct SpreadAcc<float> {
+  using type = int;  // two words per cell: hi block then lo block
 };
 
 template <typename T, int D, int CMAX>
 __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
+  using Acc = typename SpreadAcc<T>::type;
+  constexpr bool kFixed = sizeof(Acc) == 4 && sizeof(T) == 4;
+  constexpr int kWords = kFixed ? 2 : 1;  // accumulator words per cell and channel
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_count;
+  __shared__ int s_count[2];
+  __shared__ float s_red[8];
   const int TS = a.tile, TP = a.pitch, W = a.width, C = a.C;
   int lead = 1;  // cells in the leading D-1 dimensions
 #pragma unroll
   for (int q = 0; q < D - 1; ++q) lead *= TS;
   const int TV = lead * TP;  // padded tile volume
   const int PSTR = (D * W) | 1;  // odd stride of a point's kernel-value table
-  T* tile = reinterpret_cast<T*>(smem_raw);
-  T* s_psi = tile + (size_t)C * TV;                      // [kBatch][PSTR]: psi_q(j - xi_q), q-major
-  T* s_amp = s_psi + (size_t)kBatch * PSTR;              // [kBatch] alpha of the point
-  T* s_wk = s_amp + kBatch;                              // [C][kBatch]
+  Acc* tile = reinterpret_cast<Acc*>(smem_raw);           // [kWords][C][TV]
+  T* s_psi = reinterpret_cast<T*>(tile + (size_t)kWords * C * TV);  // [kBatch][PSTR]: psi_q(j - xi_q), q-major
+  T* s_wk = s_psi + (size_t)kBatch * PSTR;               // [C][kBatch]: w_k(x) alpha
   int* s_l0 = reinterpret_cast<int*>(s_wk + (size_t)C * kBatch);  // [D][kBatch]
-  int* s_pid = s_l0 + D * kBatch;                        // [kBatch] sorted point index
   const int r = blockIdx.y;
 
-  for (int i = threadIdx.x; i < C * TV; i += blockDim.x) tile[i] = T(0);
+  for (int i = threadIdx.x; i < kWords * C * TV; i += blockDim.x) tile[i] = Acc(0);
+  if (threadIdx.x == 0) s_count[0] = 0;
 
   int tc[kMaxDim] = {0, 0, 0}, base[kMaxDim] = {0, 0, 0};
   {
@@ -77,112 +108,156 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
       base[q] = tc[q] * TS;
     }
   }
-  // lane groups: one point per group; in 2-D a lane is a support row, in 3-D the
-  // warp's lanes run over the width^2 pencils, in 1-D a lane is a whole point
-  constexpr int kGroup = D == 1 ? 1 : (D == 2 ? 0 : 32);
-  const int Gs = kGroup == 0 ? W : kGroup;
-  const int ppw = 32 / Gs;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int grp = lane / Gs, gl = lane - grp * Gs;
-  int P = 1;  // pencils per point
+  // candidate ranges: bins (lead - o, last - 1 .. last) are consecutive in sorted order
+  constexpr int NR = 1 << (D - 1);
+  int rs[NR], rl[NR];
+  int total = 0;
 #pragma unroll
-  for (int q = 0; q < D - 1; ++q) P *= W;
-  const double* alpha_r = a.alpha + (size_t)r * a.n;
-
-#pragma unroll 1
-  for (int o = 0; o < (1 << (D - 1)); ++o) {
-    // bins (lead - o, last - 1 .. last) are consecutive in the sorted order
+  for (int o = 0; o < NR; ++o) {
     long long lin = 0;
     bool valid = true;
 #pragma unroll
     for (int q = 0; q < D - 1; ++q) {
-      int b = tc[q] - ((o >> q) & 1);
+      const int b = tc[q] - ((o >> q) & 1);
       valid = valid && b >= 0;
       lin = lin * a.nbins[q] + (b < 0 ? 0 : b);
     }
-    if (!valid) continue;
     const long long lin_hi = lin * a.nbins[D - 1] + tc[D - 1];
     const long long lin_lo = lin_hi - (tc[D - 1] > 0 ? 1 : 0);
-    const int r0 = a.bin_start[lin_lo], r1 = a.bin_start[lin_hi + 1];
-    for (int b0 = r0; b0 < r1; b0 += kBatch) {
-      const int nb = min(kBatch, r1 - b0);
-      __syncthreads();  // previous batch consumed (and the tile zeroed)
-      if (threadIdx.x == 0) s_count = 0;
-      __syncthreads();
-      // keep only the candidates whose support meets this tile
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        const int p = b0 + i;
-        int l0[kMaxDim];
-        bool meets = true;
+    rs[o] = valid ? a.bin_start[lin_lo] : 0;
+    rl[o] = valid ? a.bin_start[lin_hi + 1] - rs[o] : 0;
+    total += rl[o];
+  }
+  int P = 1;  // pencils per point
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
-          l0[q] = a.cell0[q][p];
-          meets = meets && l0[q] + W > base[q] && l0[q] < base[q] + TS;
-        }
-        if (meets) {
-          const int slot = atomicAdd(&s_count, 1);
+  for (int q = 0; q < D - 1; ++q) P *= W;
+  const double* alpha_r = a.alpha + (size_t)r * a.n;
+  T scale = T(1), inv_scale = T(1);
+  if (kFixed) {
+    // tile bound S = sum over the candidates reaching the tile of max_k |w_k| |alpha|
+    float part = 0.f;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      int c = i, p = 0;
 #pragma unroll
-          for (int q = 0; q < D; ++q) s_l0[q * kBatch + slot] = l0[q];
-          s_pid[slot] = p;
-          s_amp[slot] = (T)alpha_r[p];
-        }
+      for (int o = 0; o < NR; ++o) {
+        if (c >= 0 && c < rl[o]) p = rs[o] + c;
+        c -= rl[o];
       }
-      __syncthreads();
-      const int nrel = s_count;
-      for (int slot = threadIdx.x; slot < nrel; slot += blockDim.x) {
-        const int p = s_pid[slot];
-        const T* wkp = a.wk + (size_t)p * C;
+      bool meets = true;
 #pragma unroll
-        for (int k = 0; k < CMAX; ++k)
-          if (k < C) s_wk[k * kBatch + slot] = wkp[k];
-        T* psi = s_psi + slot * PSTR;
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          const T xq = a.xi[q][p];
-          for (int j = 0; j < W; ++j) psi[q * W + j] = es_psi<T>((T)j - xq, a.beta, a.inv_halfw);
-        }
+      for (int q = 0; q < D; ++q) {
+        const int l0 = a.cell0[q][p];
+        meets = meets && l0 + W > base[q] && l0 < base[q] + TS;
       }
-      __syncthreads();
-      for (int pb = warp * ppw; pb < nrel; pb += nwarps * ppw) {
-        const int i = pb + grp;
-        if (grp >= ppw || i >= nrel) continue;
-        const T* psi = s_psi + i * PSTR;
-        const int l0 = s_l0[(D - 1) * kBatch + i];
-        const int lo = max(0, base[D - 1] - l0), hi = min(W, base[D - 1] + TS - l0);
-        T wk[CMAX];
+      if (meets) part += a.wabs[p] * (float)fabs(alpha_r[p]);
+    }
 #pragma unroll
-        for (int k = 0; k < CMAX; ++k) wk[k] = k < C ? s_wk[k * kBatch + i] * s_amp[i] : T(0);
-        for (int pen = gl; pen < P; pen += Gs) {
-          int rem = pen, off = 0;
-          bool inside = true;
-          T amp = T(1);
-          int iq[kMaxDim];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    float S = 0.f;
 #pragma unroll
-          for (int q = D - 2; q >= 0; --q) {
-            iq[q] = rem % W;
-            rem /= W;
-          }
+    for (int w = 0; w < 8; ++w) S += s_red[w];
+    if (S > 0.f) {
+      int ex;
+      frexpf(S, &ex);          // S < 2^ex
+      scale = ldexpf(1.f, 38 - ex);
+      inv_scale = ldexpf(1.f, ex - 38);
+    }
+  }
+  __syncthreads();
+
+  int round = 0;
+  for (int c0 = 0; c0 < total; c0 += kBatch, ++round) {
+    const int par = round & 1;
+    const int nc = min(kBatch, total - c0);
+    // keep the candidates whose support meets this tile; their slot gets l0, the
+    // kernel values along every axis and w_k(x) alpha
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+      int c = c0 + i, p = 0;
 #pragma unroll
-          for (int q = 0; q < D - 1; ++q) {
-            const int c = s_l0[q * kBatch + i] + iq[q] - base[q];
-            inside = inside && c >= 0 && c < TS;
-            off = off * TS + c;
-            amp *= psi[q * W + iq[q]];
-          }
-          if (!inside) continue;
-          const T* plast = psi + (D - 1) * W;
-          T* rowp = tile + off * TP + (l0 - base[D - 1]);
-          for (int c = lo; c < hi; ++c) {
-            const T ps = amp * plast[c];
+      for (int o = 0; o < NR; ++o) {
+        if (c >= 0 && c < rl[o]) p = rs[o] + c;
+        c -= rl[o];
+      }
+      int l0[kMaxDim];
+      bool meets = true;
 #pragma unroll
-            for (int k = 0; k < CMAX; ++k)
-              if (k < C) atomicAdd(rowp + c + (size_t)k * TV, ps * wk[k]);
+      for (int q = 0; q < D; ++q) {
+        l0[q] = a.cell0[q][p];
+        meets = meets && l0[q] + W > base[q] && l0[q] < base[q] + TS;
+      }
+      if (!meets) continue;
+      const int slot = atomicAdd(&s_count[par], 1);
+#pragma unroll
+      for (int q = 0; q < D; ++q) s_l0[q * kBatch + slot] = l0[q];
+      T* psi = s_psi + slot * PSTR;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const T xq = a.xi[q][p];
+        for (int j = 0; j < W; ++j) psi[q * W + j] = es_psi<T>((T)j - xq, a.beta, a.inv_halfw);
+      }
+      const T amp = (T)alpha_r[p] * scale;
+      const T* wkp = a.wk + (size_t)p * C;
+#pragma unroll
+      for (int k = 0; k < CMAX; ++k)
+        if (k < C) s_wk[k * kBatch + slot] = wkp[k] * amp;
+    }
+    if (threadIdx.x == 0) s_count[par ^ 1] = 0;  // the other counter is idle this round
+    __syncthreads();
+    const int nrel = s_count[par];
+    // (slot, pencil) work items, spread evenly over the block
+    const int items = nrel * P;
+    for (int g = threadIdx.x; g < items; g += blockDim.x) {
+      const int i = (int)(((unsigned long long)g * a.pmagic) >> 24);  // g / P
+      int pen = g - i * P;
+      const T* psi = s_psi + i * PSTR;
+      int off = 0;
+      bool inside = true;
+      T amp = T(1);
+      int iq[kMaxDim];
+#pragma unroll
+      for (int q = D - 2; q >= 0; --q) {
+        const int qq = (int)(((unsigned)pen * a.wmagic) >> 12);  // pen / W
+        iq[q] = pen - qq * W;
+        pen = qq;
+      }
+#pragma unroll
+      for (int q = 0; q < D - 1; ++q) {
+        const int c = s_l0[q * kBatch + i] + iq[q] - base[q];
+        inside = inside && c >= 0 && c < TS;
+        off = off * TS + c;
+        amp *= psi[q * W + iq[q]];
+      }
+      if (!inside) continue;
+      const int l0 = s_l0[(D - 1) * kBatch + i];
+      const int lo = max(0, base[D - 1] - l0), hi = min(W, base[D - 1] + TS - l0);
+      T wk[CMAX];
+#pragma unroll
+      for (int k = 0; k < CMAX; ++k) wk[k] = k < C ? s_wk[k * kBatch + i] * amp : T(0);
+      const T* plast = psi + (D - 1) * W;
+      Acc* rowp = tile + off * TP + (l0 - base[D - 1]);
+      for (int c = lo; c < hi; ++c) {
+        const T ps = plast[c];
+#pragma unroll
+        for (int k = 0; k < CMAX; ++k) {
+          if (k < C) {
+            if constexpr (kFixed) {
+              const float v = ps * wk[k];
+              const float hf = floorf(v * (1.f / 65536.f));
+              const float lf = fmaf(-hf, 65536.f, v);
+              const int hi = __float_as_int(hf + 12582912.f) - 0x4B400000;
+              const int lo = __float_as_int(lf + 12582912.f) - 0x4B400000;
+              atomicAdd(rowp + c + (size_t)k * TV, hi);
+              atomicAdd(rowp + c + (size_t)(C + k) * TV, lo);
+            } else
+              atomicAdd(rowp + c + (size_t)k * TV, ps * wk[k]);
           }
         }
       }
     }
+    __syncthreads();  // slots are reused by the next round
   }
-  __syncthreads();
 
   // write the tile once (cells past nf in a partial last tile are dropped)
   const int vol = lead * TS;
@@ -205,8 +280,16 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
     if (!in) continue;
     T* dst = a.grid + (size_t)r * C * a.G + gidx;
 #pragma unroll
-    for (int k = 0; k < CMAX; ++k)
-      if (k < C) dst[(size_t)k * a.G] = tile[(size_t)k * TV + sidx];
+    for (int k = 0; k < CMAX; ++k) {
+      if (k < C) {
+        if constexpr (kFixed) {
+          const long long v = ((long long)tile[(size_t)k * TV + sidx] << 16) + tile[(size_t)(C + k) * TV + sidx];
+          dst[(size_t)k * a.G] = __ll2float_rn(v) * inv_scale;
+        } else {
+          dst[(size_t)k * a.G] = tile[(size_t)k * TV + sidx];
+        }
+      }
+    }
   }
 }
 
@@ -238,6 +321,7 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
     a.nbins[q] = ps.nbins[q];
   }
   a.wk = (const T*)ps.wk;
+  a.wabs = ps.wabs;
   a.bin_start = ps.bin_start;
   a.tiles = plan.active_tiles;
   a.alpha = alpha_sorted;
@@ -251,6 +335,12 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
   a.tile = g.tile;
   a.pitch = spread_pitch(g.d, g.tile);
   a.C = g.C;
+  {
+    unsigned P = 1;
+    for (int q = 0; q < g.d - 1; ++q) P *= (unsigned)g.width;
+    a.pmagic = (unsigned)(((1ull << 24) + P - 1) / P);
+    a.wmagic = (unsigned)(((1u << 12) + g.width - 1) / g.width);
+  }
   size_t smem = spread_smem_bytes(g.d, g.tile, g.C, sizeof(T), g.width);
   dim3 grid((unsigned)plan.n_active_tiles, (unsigned)R);
   switch (g.d) {
@@ -268,8 +358,8 @@ int spread_pitch(int d, int tile) { return d == 1 ? tile : tile + 1; }
 size_t spread_smem_bytes(int d, int tile, int C, size_t rs, int width) {
   size_t lead = 1;
   for (int q = 0; q < d - 1; ++q) lead *= tile;
-  size_t tilev = lead * spread_pitch(d, tile) * (size_t)C * rs;
-  size_t batch = (size_t)kBatch * ((((size_t)d * width) | 1) * rs + (1 + C) * rs + (d + 1) * sizeof(int));
+  size_t tilev = lead * spread_pitch(d, tile) * (size_t)C * 8;  // two int32 words (FP32) or one double
+  size_t batch = (size_t)kBatch * ((((size_t)d * width) | 1) * rs + C * rs + d * sizeof(int));
   return tilev + batch;
 }
 
