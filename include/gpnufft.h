@@ -172,6 +172,31 @@ int gp_cg_solve_refined(gp_plan_t plan_lo, gp_plan_t plan_hi, const double* y, d
 int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, long long Nq, const double* field_aq,
                       const double* field_bq, double* mu, void* cuda_stream);
 
+/* Largest query batch of gp_posterior_mean_noalloc (sizes its static scratch). */
+#define GP_NOALLOC_MAX_QUERIES 32768
+
+/* gp_posterior_mean without any device allocation.  The paper has no counterpart:
+ * it is a serving form of the same result (Eq. postmean), for callers that must not
+ * allocate while they run, such as a serving loop that shares the device with
+ * other streams (cudaFree synchronises the whole device) or a process that has
+ * committed the device memory up front.
+ *   Arguments as gp_posterior_mean, with 1 <= Nq <= GP_NOALLOC_MAX_QUERIES (else
+ *   GP_EINVAL, nothing launched).  Host or device pointers; host inputs and a host
+ *   mu are staged through a static device array of 256 + 48 * GP_NOALLOC_MAX_QUERIES
+ *   bytes (about 1.5 MB) per device, and the rest of the work uses buffers the
+ *   plan already holds.  Each query is evaluated straight from the fine grid
+ *   (no binning), so large batches are better served by gp_posterior_mean.
+ *   Queries outside the plan box or sigma range get mu = NaN and the call
+ *   returns GP_EINVAL after the others are written.
+ * The first call on each device does a one-time set-up (it looks up the device
+ * address of the static array, with the plan's device current); make that first
+ * call before any stream capture begins.  The static array is shared by all calls
+ * on a device: calls whose GPU work overlaps (other streams, other host threads,
+ * other plans) race on it.  The call waits for its stream before returning.
+ * Errors: GP_EINVAL, GP_ECUDA, GP_ECUFFT, GP_ETIMEOUT. */
+int gp_posterior_mean_noalloc(gp_plan_t plan, const double* alpha, const double* xq, long long Nq,
+                              const double* field_aq, const double* field_bq, double* mu, void* cuda_stream);
+
 /* Per-phase timing of the matvec, with CUDA events recorded on the stream each
  * phase is launched on.  gp_profile_enable(plan, 1) clears the counters and starts
  * recording around every later matvec of this plan (gp_matvec, each CG iteration,

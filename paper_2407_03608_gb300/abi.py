@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgpnufft.so")
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ECUFFT, GP_ENOTCONV, GP_EBREAKDOWN, GP_ETIMEOUT, GP_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 GP_FP64, GP_FP32 = 0, 1
+GP_NOALLOC_MAX_QUERIES = 32768
 GP_MATERN, GP_SE = 0, 1
 GP_PARAMS_SCALES, GP_PARAMS_PAPER = 0, 1
 GP_SET_NT, GP_SET_NSIGMA, GP_SET_SIGMA_RANGE, GP_SET_M, GP_SET_DW, GP_SET_NUFFT, GP_SET_BOX, GP_SET_NF, GP_SET_TILE = \
@@ -32,7 +33,7 @@ STATUS_NAMES = {0: "GP_OK", -1: "GP_EINVAL", -2: "GP_ENOMEM", -3: "GP_ECUDA", -4
 
 #: every symbol include/gpnufft.h declares
 EXPORTED = ["gp_plan_opts_default", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined",
-            "gp_posterior_mean", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
+            "gp_posterior_mean", "gp_posterior_mean_noalloc", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
             "gp_version"]
 
 
@@ -90,6 +91,8 @@ def _load():
     lib.gp_cg_solve_refined.restype = ctypes.c_int
     lib.gp_posterior_mean.argtypes = [vp, dp, dp, ctypes.c_longlong, dp, dp, dp, vp]
     lib.gp_posterior_mean.restype = ctypes.c_int
+    lib.gp_posterior_mean_noalloc.argtypes = [vp, dp, dp, ctypes.c_longlong, dp, dp, dp, vp]
+    lib.gp_posterior_mean_noalloc.restype = ctypes.c_int
     lib.gp_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.gp_profile_enable.restype = ctypes.c_int
     lib.gp_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -216,6 +219,18 @@ def gp_posterior_mean(plan, alpha, xq, field_aq, field_bq, mu, stream=None):
     mp, mk = ptr_of(mu)
     return check(LIB.gp_posterior_mean(plan, ap, qp, int(xq.shape[0]), fa, fb, mp,
                                        stream if stream is not None else current_stream()))
+
+
+def gp_posterior_mean_noalloc(plan, alpha, xq, field_aq, field_bq, mu, stream=None):
+    """Posterior mean through the entry point that allocates no device memory (at most
+    GP_NOALLOC_MAX_QUERIES queries); mu must be preallocated by the caller."""
+    ap, ak = ptr_of(alpha)
+    qp, qk = ptr_of(xq)
+    fa, fak = ptr_of(field_aq)
+    fb, fbk = ptr_of(field_bq)
+    mp, mk = ptr_of(mu)
+    return check(LIB.gp_posterior_mean_noalloc(plan, ap, qp, int(xq.shape[0]), fa, fb, mp,
+                                               stream if stream is not None else current_stream()))
 
 
 def gp_profile_enable(plan, on: bool):

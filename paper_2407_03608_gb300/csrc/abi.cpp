@@ -587,6 +587,48 @@ int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, lon
   });
 }
 
+int gp_posterior_mean_noalloc(gp_plan_t plan, const double* alpha, const double* xq, long long Nq,
+                              const double* field_aq, const double* field_bq, double* mu, void* cuda_stream) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    GPN_CHECK(alpha && xq && field_aq && field_bq && mu, GP_EINVAL, "null argument");
+    GPN_CHECK(Nq >= 1 && Nq <= GP_NOALLOC_MAX_QUERIES, GP_EINVAL,
+              "Nq must be in [1, " + std::to_string(GP_NOALLOC_MAX_QUERIES) +
+                  "]: the static scratch of gp_posterior_mean_noalloc holds that many queries");
+    const int d = p->h.d;
+    unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch(p->device));
+    unsigned* bad = reinterpret_cast<unsigned*>(scratch);
+    double* stage = reinterpret_cast<double*>(scratch + kNoAllocHeaderBytes);
+    double* sx = stage;
+    double* sa = sx + (size_t)Nq * d;
+    double* sb = sa + Nq;
+    double* smu = sb + Nq;
+    GPN_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), st));  // the counter starts at zero every call
+    const double* x = dev_input(xq, sx, (size_t)Nq * d, st);
+    const double* fa = dev_input(field_aq, sa, (size_t)Nq, st);
+    const double* fb = dev_input(field_bq, sb, (size_t)Nq, st);
+    DevOut o(mu, smu, (size_t)Nq);
+    const double* al = dev_input(alpha, p->stage_in, (size_t)p->N, st);
+    gather_sorted(p->pts, al, p->vec_a, 1, st);
+    launch_spread(*p, p->vec_a, 1, st);
+    run_fft_forward(*p, 1, st);
+    launch_diag(*p, 1, st);
+    run_fft_inverse(*p, 1, st);
+    launch_query_interp(*p, x, fa, fb, Nq, o.dev, bad, st);
+    if (o.host) GPN_CUDA(cudaMemcpyAsync(o.host, o.dev, sizeof(double) * Nq, cudaMemcpyDeviceToHost, st));
+    check_device_status(*p, st);  // also waits for the stream
+    GPN_CUDA(cudaMemcpyAsync(p->host_status, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    GPN_CUDA(cudaStreamSynchronize(st));
+    const int nbad = *p->host_status;
+    *p->host_status = 0;
+    GPN_CHECK(nbad == 0, GP_EINVAL,
+              std::to_string((unsigned)nbad) + " queries outside the plan box or sigma range (mu is NaN there)");
+    return GP_OK;
+  });
+}
+
 int gp_profile_enable(gp_plan_t plan, int on) {
   return guarded([&]() {
     Plan* p = as_plan(plan);
