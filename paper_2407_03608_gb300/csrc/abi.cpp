@@ -360,6 +360,7 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   std::vector<int> bstart;
   build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
   build_active_tiles(*plan, bstart);
+  if (spread2d_supported(*plan)) build_spread2d_tiles(*plan, bstart);
   plan->a_tensor = plan->alloc((size_t)(C * (C + 1) / 2) * nfreq * rs);
   build_a_tensor(*plan, st);
   plan->grid = plan->alloc((size_t)C * max_rhs * G * rs);

@@ -75,6 +75,8 @@ struct Plan {
   void* grid_out = nullptr;             // C2R output read by interp, same shape
   int* active_tiles = nullptr;          // tiles some point's support reaches
   long long n_active_tiles = 0;
+  int* sp2_tiles = nullptr;             // 2-D register-accumulating spread: active 16 x TY tiles
+  long long n_sp2_tiles = 0;
   int interp_cc = 1;                    // channels per interp staging chunk
   CUtensorMap tmap_out;                 // TMA descriptor of grid_out (d >= 2)
   int* dev_status = nullptr;            // set by kernels whose bounded waits ran out
@@ -154,6 +156,11 @@ size_t interp_stage_bytes(int d, int tile, int width, size_t rs);
 // Steps (1)+(2a): spread sorted-order coefficients alpha (N x R, float64) onto the
 // fine grids (C * R channels).
 void launch_spread(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st);
+// 2-D spreading with register accumulators (used when supported for the plan)
+bool spread2d_supported(const Plan& plan);
+int spread2d_rows(const Plan& plan);
+void build_spread2d_tiles(Plan& plan, const std::vector<int>& bstart);
+void launch_spread2d(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st);
 // Steps (2b)+(3)+(4a): deconvolve, apply A', zero outside the mode box (in spec).
 void launch_diag(Plan& plan, int R, cudaStream_t st);
 // Steps (4b)+(5): interpolate at the points of ps and combine channels:

@@ -364,6 +364,7 @@ size_t spread_smem_bytes(int d, int tile, int C, size_t rs, int width) {
 }
 
 void launch_spread(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
+  if (plan.sp2_tiles) return launch_spread2d(plan, alpha_sorted, R, st);
   if (plan.precision == GP_FP32)
     spread_impl<float>(plan, alpha_sorted, R, st);
   else
