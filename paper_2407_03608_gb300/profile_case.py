@@ -1,0 +1,40 @@
+"""A fixed workload for profilers: a few matvecs of one plan on the 2-D clustered points.
+
+    python -m paper_2407_03608_gb300.profile_case --eps 1e-5 [--n 1000000] [--precision fp32] [--matvecs 4]
+
+Builds the plan for the synthetic 2-D workload (half uniform, half in eight Gaussian
+clusters, Matern 3/2), runs ``--matvecs`` matvecs and prints the plan sizes.  It does
+nothing else, so an ncu launch filter (``-k``, ``-s``, ``-c``) sees only the plan build
+and the matvec kernels.
+"""
+import argparse
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--eps", type=float, default=1e-5)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--matvecs", type=int, default=4)
+    ap.add_argument("--transform", type=int, default=0)
+    args = ap.parse_args()
+    import torch
+    import gpinputs
+    import paper_2407_03608_gb300 as gpn
+    w = gpinputs.config_2d(args.n, 1.5)
+    dev = torch.device("cuda", 0)
+    prec = gpn.GP_FP32 if args.precision == "fp32" else gpn.GP_FP64
+    plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
+                    torch.from_numpy(w.l).to(dev), nu=1.5, eps=args.eps, precision=prec,
+                    transform=args.transform)
+    a = torch.from_numpy(w.alpha).to(dev)
+    out = None
+    for _ in range(args.matvecs):
+        out = plan.matvec(a)
+    torch.cuda.synchronize()
+    i = plan.info
+    print({k: i[k] for k in ("nf", "M", "n_sigma", "kernel_width", "tile", "transform")}, float(out.norm()))
+
+
+if __name__ == "__main__":
+    main()
