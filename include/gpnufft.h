@@ -90,10 +90,14 @@ typedef struct gp_plan_opts {
   double box_lo[3], box_hi[3];
   long long nf;
   int tile;
-  int transform;          /* 0 auto (2 for GP_FP64 when supported, else 1);
+  int transform;          /* 0 auto (3 for d = 2 when nf = 2^a; 2 for d = 1 in FP64;
+                               else 1);
                              1 full-grid cuFFT R2C/C2R;
                              2 pruned: custom shared-memory row FFTs keeping modes 0..M,
-                               cuFFT along the first axis (d <= 2, nf = 2^a)             */
+                               cuFFT along the first axis (d <= 2, nf = 2^a);
+                             3 pruned, transposed (d = 2, nf = 2^a): custom row FFTs
+                               write columns of modes 0..M, cuFFT transforms each
+                               contiguous column, step 3 on the mode box only    */
   int max_rhs;            /* largest R the plan will be called with (default 1)         */
   long long max_bytes;    /* refuse plans whose resident device bytes exceed this (0 = no limit) */
 } gp_plan_opts;
@@ -107,7 +111,7 @@ typedef struct gp_plan_info {
   int kernel_width; double kernel_beta;    /* exponential-of-semicircle spreading kernel  */
   double upsampfac; double nufft_tol;
   int tile;                                /* spread/interp tile edge (cells)             */
-  int transform;                           /* transform mode in use (1 or 2)              */
+  int transform;                           /* transform mode in use (1, 2 or 3)           */
   double box_lo[3], box_hi[3];             /* region points and queries must lie in       */
   double est_err_t, est_err_sigma, est_err_trunc, est_err_alias; /* stage estimates, relative entrywise */
   long long bytes_resident;                /* device bytes the plan holds                 */

@@ -136,6 +136,7 @@ Plan::~Plan() {
   for (auto& kv : fft_fwd) cufftDestroy(kv.second);
   for (auto& kv : fft_inv) cufftDestroy(kv.second);
   for (auto& kv : fft_col) cufftDestroy(kv.second);
+  for (auto& kv : fft_t3) cufftDestroy(kv.second);
   for (void* p : owned) cudaFree(p);
   if (host_scal) cudaFreeHost(host_scal);
   if (host_status) cudaFreeHost(host_status);
@@ -361,19 +362,26 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
   build_active_tiles(*plan, bstart);
   if (spread2d_supported(*plan)) build_spread2d_tiles(*plan, bstart);
+  GPN_CHECK(o.transform >= 0 && o.transform <= 3, GP_EINVAL, "transform must be 0, 1, 2 or 3");
+  const bool row_ok = rowfft_supported(d, h.nf, rs);
+  const bool t3_ok = tr3_supported(d, h.nf, rs);
+  GPN_CHECK(o.transform != 2 || row_ok, GP_EUNSUPPORTED, "pruned row transforms need d <= 2 and power-of-two nf");
+  GPN_CHECK(o.transform != 3 || t3_ok, GP_EUNSUPPORTED, "transposed pruned transforms need d = 2 and nf = 2^a");
+  // auto: the transposed pruned transforms for d = 2; the pruned row transforms for
+  // d = 1 in FP64 (FP64 FFT arithmetic is ALU-bound on GB300); else full-grid cuFFT
+  plan->tr3 = o.transform == 3 || (o.transform == 0 && t3_ok);
+  plan->rowfft = o.transform == 2 || (o.transform == 0 && !plan->tr3 && row_ok && o.precision == GP_FP64);
+  if (plan->tr3) {
+    nfreq = (h.M + 1) * (h.M + 1);
+    plan->n_freq = nfreq;
+  }
   plan->a_tensor = plan->alloc((size_t)(C * (C + 1) / 2) * nfreq * rs);
   build_a_tensor(*plan, st);
   plan->grid = plan->alloc((size_t)C * max_rhs * G * rs);
   GPN_CUDA(cudaMemsetAsync(plan->grid, 0, (size_t)C * max_rhs * G * rs, st));
   plan->grid_out = plan->alloc((size_t)C * max_rhs * G * rs);
   GPN_CUDA(cudaMemsetAsync(plan->grid_out, 0, (size_t)C * max_rhs * G * rs, st));
-  GPN_CHECK(o.transform >= 0 && o.transform <= 2, GP_EINVAL, "transform must be 0, 1 or 2");
-  const bool row_ok = rowfft_supported(d, h.nf, rs);
-  GPN_CHECK(o.transform != 2 || row_ok, GP_EUNSUPPORTED, "pruned row transforms need d <= 2 and power-of-two nf");
-  // auto: the pruned transforms remove FP64 FFT arithmetic (ALU-bound on GB300);
-  // in FP32 the full-grid cuFFT plans are the faster choice (measured)
-  plan->rowfft = o.transform == 2 || (o.transform == 0 && row_ok && o.precision == GP_FP64);
-  if (plan->rowfft) {
+  if (plan->rowfft || plan->tr3) {
     set_data_extent(*plan);
     const size_t rows = d == 2 ? (size_t)h.nf : 1;
     const size_t fbytes = rows * C * (size_t)max_rhs * (h.M + 1) * 2 * rs;
@@ -382,7 +390,10 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
     plan->fz = plan->alloc(fbytes);
     GPN_CUDA(cudaMemsetAsync(plan->fx, 0, fbytes, st));
     GPN_CUDA(cudaMemsetAsync(plan->fz, 0, fbytes, st));
-    build_twiddles(*plan);
+    if (plan->tr3)
+      tr3_setup(*plan);
+    else
+      build_twiddles(*plan);
   } else {
     plan->spec = plan->alloc((size_t)C * max_rhs * S * 2 * rs);
   }
@@ -405,7 +416,9 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->scal = (double*)plan->alloc(sizeof(double) * 8 * max_rhs);
   plan->partials = (double*)plan->alloc(sizeof(double) * 512 * max_rhs);
   GPN_CUDA(cudaMallocHost(&plan->host_scal, sizeof(double) * 8 * max_rhs));
-  if (plan->rowfft) {
+  if (plan->tr3) {
+    plan->t3_plan(1);
+  } else if (plan->rowfft) {
     if (d == 2) plan->col_plan(1);
   } else {
     plan->fwd_plan(1);
@@ -684,7 +697,7 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->upsampfac = h.upsamp;
     info->nufft_tol = h.nufft_tol;
     info->tile = h.tile;
-    info->transform = p->rowfft ? 2 : 1;
+    info->transform = p->tr3 ? 3 : (p->rowfft ? 2 : 1);
     for (int q = 0; q < 3; ++q) {
       info->box_lo[q] = h.box_lo[q];
       info->box_hi[q] = h.box_hi[q];

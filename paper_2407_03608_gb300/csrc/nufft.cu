@@ -27,6 +27,7 @@ struct ATensorArgs {
   int C;
   int J;
   int d;
+  int quad;             // 1: d = 2 quadrant layout [pair][m_1][m_0], m_a = 0..M
 };
 
 __global__ void k_build_a_f32(ATensorArgs<float> a);
@@ -38,12 +39,17 @@ __device__ void build_a_body(const ATensorArgs<T>& a) {
   if (f >= a.n_freq) return;
   long long m[kMaxDim];
   long long rest = f;
-  m[a.d - 1] = rest % (a.M + 1);
-  rest /= (a.M + 1);
-  for (int q = a.d - 2; q >= 0; --q) {
-    long long v = rest % (2 * a.M + 1) - a.M;
-    rest /= (2 * a.M + 1);
-    m[q] = v < 0 ? -v : v;
+  if (a.quad) {
+    m[0] = rest % (a.M + 1);
+    m[1] = rest / (a.M + 1);
+  } else {
+    m[a.d - 1] = rest % (a.M + 1);
+    rest /= (a.M + 1);
+    for (int q = a.d - 2; q >= 0; --q) {
+      long long v = rest % (2 * a.M + 1) - a.M;
+      rest /= (2 * a.M + 1);
+      m[q] = v < 0 ? -v : v;
+    }
   }
   const long long Mp = a.M + 1;
   int p = 0;
@@ -81,10 +87,10 @@ void build_a_tensor(Plan& plan, cudaStream_t st) {
   if (e == cudaSuccess) {
     int nb = blocks_for(plan.n_freq, 128);
     if (plan.precision == GP_FP32) {
-      ATensorArgs<float> a{etab, vt, (float*)plan.a_tensor, plan.n_freq, h.M, C, J, h.d};
+      ATensorArgs<float> a{etab, vt, (float*)plan.a_tensor, plan.n_freq, h.M, C, J, h.d, plan.tr3 ? 1 : 0};
       k_build_a_f32<<<nb, 128, 0, st>>>(a);
     } else {
-      ATensorArgs<double> a{etab, vt, (double*)plan.a_tensor, plan.n_freq, h.M, C, J, h.d};
+      ATensorArgs<double> a{etab, vt, (double*)plan.a_tensor, plan.n_freq, h.M, C, J, h.d, plan.tr3 ? 1 : 0};
       k_build_a_f64<<<nb, 128, 0, st>>>(a);
     }
     e = cudaGetLastError();
@@ -124,6 +130,7 @@ cufftHandle Plan::inv_plan(int R) {
 }
 
 void run_fft_forward(Plan& plan, int R, cudaStream_t st) {
+  if (plan.tr3) return tr3_forward(plan, R, st);
   if (plan.rowfft) return rowfft_forward(plan, R, st);
   cufftHandle h = plan.fwd_plan(R);
   GPN_CUFFT(cufftSetStream(h, st));
@@ -134,6 +141,7 @@ void run_fft_forward(Plan& plan, int R, cudaStream_t st) {
 }
 
 void run_fft_inverse(Plan& plan, int R, cudaStream_t st) {
+  if (plan.tr3) return tr3_inverse(plan, R, st);
   if (plan.rowfft) return rowfft_inverse(plan, R, st);
   cufftHandle h = plan.inv_plan(R);
   GPN_CUFFT(cufftSetStream(h, st));

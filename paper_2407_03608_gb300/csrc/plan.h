@@ -109,6 +109,13 @@ struct Plan {
   int col_lo = 0, col_hi = 0;           // grid columns holding data or read by interp (last axis)
   std::map<int, cufftHandle> fft_col;   // first-axis C2C plans keyed by R
   cufftHandle col_plan(int R);
+  // transposed pruned path (transform 3, d = 2): fx, fy, fz hold [cr][M+1][nf] columns,
+  // the A' tensor is stored on the quadrant [pair][m][|n1|]
+  bool tr3 = false;
+  int t3_rb = 1;                        // grid rows per CTA of the row kernels
+  void* tw_half = nullptr;              // two-level twiddle tables of the row kernels
+  std::map<int, cufftHandle> fft_t3;    // contiguous column C2C plans keyed by R
+  cufftHandle t3_plan(int R);
   long long bytes = 0;
   std::vector<void*> owned;             // every cudaMalloc of the plan
 
@@ -191,6 +198,12 @@ void build_twiddles(Plan& plan);
 void rowfft_forward(Plan& plan, int R, cudaStream_t st);
 void rowfft_diag(Plan& plan, int R, cudaStream_t st);
 void rowfft_inverse(Plan& plan, int R, cudaStream_t st);
+// transposed pruned transforms (d = 2, nf = 2^a)
+bool tr3_supported(int d, long long nf, size_t rs);
+void tr3_setup(Plan& plan);
+void tr3_forward(Plan& plan, int R, cudaStream_t st);
+void tr3_diag(Plan& plan, int R, cudaStream_t st);
+void tr3_inverse(Plan& plan, int R, cudaStream_t st);
 
 // Full matvec in sorted order: out = (K~ + shift I) alpha.
 void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st);

@@ -1,0 +1,96 @@
+// Host driver for tests/test_fft_core.py: runs the row-FFT building blocks of
+// csrc/fft_core.h on the CPU, with the same pass schedule as the device kernels
+// (one pass of radix 2^(L mod 4) first when L is not a multiple of 4, then radix-16
+// passes), emulating the block barrier between the load and store halves of a pass.
+//
+// stdin:  mode L count, then the input numbers (mode c2c/ic2c: 2*2^L reals as
+//         interleaved complex; r2c: 2^(L+1) reals; c2r: 2*(2^L + 1) reals, the half
+//         spectrum X[0..N2]).
+// stdout: the output numbers, one per line (c2c/ic2c: 2*2^L; r2c: 2*(2^L + 1);
+//         c2r: 2^(L+1) reals).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "fft_core.h"
+
+using gpn::fft::cpx;
+using gpn::fft::Pass;
+using C = cpx<double>;
+
+template <int R, int NB, bool INV>
+void pass(std::vector<C>& buf, const std::vector<C>& tw, int N, int Ns) {
+  const int nt = N / 16;
+  std::vector<Pass<R, NB, double>> st(nt);
+  for (int t = 0; t < nt; ++t) st[t].load(buf.data(), N, t, nt);
+  // the two-level twiddle of the device kernels
+  std::vector<C> hi(N / 64 + 1), lo(64);
+  for (int q = 0; q < (int)hi.size(); ++q) hi[q] = tw[(64 * q) % N];
+  for (int j = 0; j < 64; ++j) lo[j] = {std::cos(2 * M_PI * j / N), -std::sin(2 * M_PI * j / N)};
+  const gpn::fft::Twiddle2<double> t2{hi.data(), lo.data()};
+  for (int t = 0; t < nt; ++t) st[t].template store<INV>(buf.data(), t2, N, Ns, t, nt);
+}
+
+template <bool INV>
+void fft(std::vector<C>& buf, int L) {
+  const int N = 1 << L;
+  std::vector<C> tw(N);
+  for (int i = 0; i < N; ++i) tw[i] = {std::cos(2 * M_PI * i / N), -std::sin(2 * M_PI * i / N)};
+  int Ns = 1;
+  switch (L % 4) {
+    case 1: pass<2, 8, INV>(buf, tw, N, Ns); Ns *= 2; break;
+    case 2: pass<4, 4, INV>(buf, tw, N, Ns); Ns *= 4; break;
+    case 3: pass<8, 2, INV>(buf, tw, N, Ns); Ns *= 8; break;
+    default: break;
+  }
+  for (int q = 0; q < L / 4; ++q) {
+    pass<16, 1, INV>(buf, tw, N, Ns);
+    Ns *= 16;
+  }
+}
+
+int main() {
+  char mode[16];
+  int L;
+  if (std::scanf("%15s %d", mode, &L) != 2) return 1;
+  const int N = 1 << L;
+  std::vector<C> buf(gpn::fft::pad(N) + 1, C{0, 0});
+  auto at = [&](int i) -> C& { return buf[gpn::fft::pad(i)]; };
+  std::vector<C> wnf(N + 1);
+  for (int k = 0; k <= N; ++k) wnf[k] = {std::cos(M_PI * k / N), -std::sin(M_PI * k / N)};  // W_{2N}^k
+  if (!std::strcmp(mode, "c2c") || !std::strcmp(mode, "ic2c")) {
+    for (int i = 0; i < N; ++i) {
+      double re, im;
+      if (std::scanf("%lf %lf", &re, &im) != 2) return 1;
+      at(i) = {re, im};
+    }
+    if (mode[0] == 'i')
+      fft<true>(buf, L);
+    else
+      fft<false>(buf, L);
+    for (int i = 0; i < N; ++i) std::printf("%.17g\n%.17g\n", at(i).x, at(i).y);
+  } else if (!std::strcmp(mode, "r2c")) {
+    for (int i = 0; i < N; ++i) {
+      double a, b;
+      if (std::scanf("%lf %lf", &a, &b) != 2) return 1;
+      at(i) = {a, b};  // z[n] = x[2n] + i x[2n+1]
+    }
+    fft<false>(buf, L);
+    for (int k = 0; k <= N; ++k) {
+      const C z = at(k % N), zn = at((N - k) % N);
+      const C X = gpn::fft::r2c_split(z, zn, wnf[k]);
+      std::printf("%.17g\n%.17g\n", X.x, X.y);
+    }
+  } else if (!std::strcmp(mode, "c2r")) {
+    std::vector<C> X(N + 1);
+    for (int k = 0; k <= N; ++k)
+      if (std::scanf("%lf %lf", &X[k].x, &X[k].y) != 2) return 1;
+    for (int k = 0; k < N; ++k) at(k) = gpn::fft::c2r_merge(X[k], X[N - k], wnf[k]);
+    fft<true>(buf, L);
+    for (int n = 0; n < N; ++n) std::printf("%.17g\n%.17g\n", at(n).x, at(n).y);
+  } else {
+    return 1;
+  }
+  return 0;
+}

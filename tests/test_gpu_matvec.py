@@ -64,11 +64,14 @@ CASES = [
 
 @pytest.mark.parametrize("d,n,nu,n_t,n_sigma,M", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("transform", [1, 2])
+@pytest.mark.parametrize("transform", [1, 2, 3])
 def test_matvec_vs_exact_nudft(gpn, d, n, nu, n_t, n_sigma, M, precision, transform):
-    """transform 1: full-grid cuFFT R2C/C2R; 2: pruned row transforms (d <= 2)."""
+    """transform 1: full-grid cuFFT R2C/C2R; 2: pruned row transforms (d <= 2);
+    3: pruned transposed transforms (d = 2)."""
     if transform == 2 and d == 3:
         pytest.skip("pruned row transforms cover d <= 2")
+    if transform == 3 and d != 2:
+        pytest.skip("transposed transforms cover d = 2")
     w = small_case(d, n, 0)
     X = w.points
     wp, sig = okern.paper_fields(w.s, w.l, d)
@@ -94,7 +97,7 @@ def test_matvec_host_pointers_match_device(gpn):
     assert rel(host, dev) < 1e-14
 
 
-@pytest.mark.parametrize("transform", [1, 2])
+@pytest.mark.parametrize("transform", [1, 2, 3])
 def test_matvec_multi_rhs_equals_columns(gpn, transform):
     w = gpinputs.config_2d(800, 1.5)
     plan = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-4, max_rhs=3, transform=transform)
@@ -106,7 +109,7 @@ def test_matvec_multi_rhs_equals_columns(gpn, transform):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("transform", [2])
+@pytest.mark.parametrize("transform", [2, 3])
 def test_pruned_transforms_match_full_grid(gpn, precision, transform):
     """The pruned row/column transforms compute the same K~ alpha as the full 2-D cuFFT path,
     on repeated calls with different inputs (zero regions must stay zero)."""
