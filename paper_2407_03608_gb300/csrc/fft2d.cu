@@ -51,8 +51,10 @@ struct Vec2<double> {
 // RB adjacent complex values to global memory (16-byte stores where possible)
 template <typename T, int RB>
 __device__ __forceinline__ void store_rb(cpx<T>* o, const cpx<T> (&v)[RB]) {
-  if constexpr (sizeof(T) == 4 && RB == 2) {
-    *reinterpret_cast<float4*>(o) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  if constexpr (sizeof(T) == 4 && RB % 2 == 0) {
+#pragma unroll
+    for (int r = 0; r < RB; r += 2)
+      *reinterpret_cast<float4*>(o + r) = make_float4(v[r].x, v[r].y, v[r + 1].x, v[r + 1].y);
   } else {
 #pragma unroll
     for (int r = 0; r < RB; ++r) *reinterpret_cast<typename Vec2<T>::type*>(o + r) = {v[r].x, v[r].y};
@@ -61,10 +63,13 @@ __device__ __forceinline__ void store_rb(cpx<T>* o, const cpx<T> (&v)[RB]) {
 
 template <typename T, int RB>
 __device__ __forceinline__ void load_rb(const cpx<T>* o, cpx<T> (&v)[RB]) {
-  if constexpr (sizeof(T) == 4 && RB == 2) {
-    const float4 u = *reinterpret_cast<const float4*>(o);
-    v[0] = {u.x, u.y};
-    v[1] = {u.z, u.w};
+  if constexpr (sizeof(T) == 4 && RB % 2 == 0) {
+#pragma unroll
+    for (int r = 0; r < RB; r += 2) {
+      const float4 u = *reinterpret_cast<const float4*>(o + r);
+      v[r] = {u.x, u.y};
+      v[r + 1] = {u.z, u.w};
+    }
   } else {
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
@@ -74,20 +79,31 @@ __device__ __forceinline__ void load_rb(const cpx<T>* o, cpx<T> (&v)[RB]) {
   }
 }
 
-// shared-memory elements of one row buffer: the padded length-N2 FFT plus the slot N2
-__host__ __device__ constexpr int row_buf(int n2) { return n2 + n2 / 16 + 1; }
+// shared-memory elements of one row buffer: the padded length-N2 FFT plus the slot N2,
+// rounded up to an even count (16-byte alignment of what follows)
+__host__ __device__ constexpr int row_buf(int n2) { return (n2 + n2 / 16 + 2) & ~1; }
 // entries of one high-part twiddle table (W^{64 q}, q <= N2 / 64)
 __host__ __device__ constexpr int tw_hi(int n2) { return n2 / 64 + 1; }
-// dynamic shared memory of a row kernel: RB row buffers, then the two-level twiddles of
-// the length-N2 FFT ([hi][lo]) and of the real split ([hi][lo])
-constexpr size_t row_smem(int n2, int rb, size_t cs) { return ((size_t)rb * row_buf(n2) + 2 * (tw_hi(n2) + 64)) * cs; }
-
-// the twiddle functors over the tables staged in shared memory
-template <typename T>
-__device__ __forceinline__ void stage_twiddles(cpx<T>* s_tw, const cpx<T>* __restrict__ g, int n2) {
-  for (int i = threadIdx.x; i < 2 * (tw_hi(n2) + 64); i += blockDim.x) s_tw[i] = g[i];
+// The FP32 forward kernel reads per-pass twiddle tables (fft::pass_tables) staged in
+// shared memory, one load a twiddle; the others form the FFT twiddles from the
+// two-level tables (measured: the inverse kernel runs faster with the smaller
+// shared-memory footprint).
+template <typename T, bool INV>
+__host__ __device__ constexpr bool pass_tables_in_smem() { return sizeof(T) == 4 && !INV; }
+// twiddle entries staged by a row kernel: the two-level tables of the length-N2 FFT
+// ([hi][lo]) and of the real split ([hi][lo]), then (FP32) the pass tables; padded to
+// whole 16-byte chunks
+template <typename T, bool INV>
+__host__ __device__ constexpr int tw_count(int L) {
+  return (2 * (tw_hi(1 << L) + 64) + (pass_tables_in_smem<T, INV>() ? fft::pass_table_size(L) : 0) + 1) & ~1;
+}
+// dynamic shared memory of a row kernel: RB row buffers, then the twiddles
+template <typename T, bool INV>
+constexpr size_t row_smem(int L, int rb) {
+  return ((size_t)rb * row_buf(1 << L) + tw_count<T, INV>(L)) * sizeof(cpx<T>);
 }
 
+// the twiddle functors over the tables staged in shared memory
 template <typename T>
 struct RowsArgs {
   const T* gin;            // spreading grids (forward input), (R*C) x nf x nf
@@ -97,15 +113,18 @@ struct RowsArgs {
   long long nf;
   long long G;             // nf^2
   int M;
-  int row0;                // first row of block 0 (a multiple of RB)
+  int row0;                // first row of item 0 (a multiple of RB)
   int row_hi;
+  long long npairs;        // RB-row groups per grid
+  long long nitems;        // npairs * C * R
   int col_lo, col_hi;
 };
 
 // In-place complex FFT of length 2^L on the row buffer b, NT = 2^L / 16 threads per
-// row (t = 0..NT-1), every thread of the block taking part in the barriers.
+// row (t = 0..NT-1), every thread of the block taking part in the barriers.  tw2: the
+// two-level twiddle of the length-2^L FFT; ptab: the staged pass tables (FP32).
 template <bool INV, int L, typename T>
-__device__ __forceinline__ void fft_block(cpx<T>* b, const fft::Twiddle2<T>& tw, int t) {
+__device__ __forceinline__ void fft_block(cpx<T>* b, const fft::Twiddle2<T>& tw2, const cpx<T>* ptab, int t) {
   constexpr int N = 1 << L, NT = N / 16;
   int Ns = 1;
   if constexpr (L % 4 != 0) {
@@ -113,69 +132,108 @@ __device__ __forceinline__ void fft_block(cpx<T>* b, const fft::Twiddle2<T>& tw,
     fft::Pass<R, 16 / R, T> p;
     p.load(b, N, t, NT);
     __syncthreads();
-    p.template store<INV>(b, tw, N, Ns, t, NT);
+    p.template store<INV>(b, tw2, N, Ns, t, NT);  // span 1: no twiddles
     __syncthreads();
     Ns *= R;
   }
-#pragma unroll 1
+#pragma unroll
   for (int s = 0; s < L / 4; ++s) {
     fft::Pass<16, 1, T> p;
     p.load(b, N, t, NT);
     __syncthreads();
-    p.template store<INV>(b, tw, N, Ns, t, NT);
+    if constexpr (pass_tables_in_smem<T, INV>()) {
+      const fft::PassTwiddle<T> tw{ptab + fft::pass_table_offset(L, Ns), Ns};
+      p.template store<INV>(b, tw, N, Ns, t, NT);
+    } else {
+      p.template store<INV>(b, tw2, N, Ns, t, NT);
+    }
     __syncthreads();
     Ns *= 16;
   }
 }
 
-// Blocks of RB * 2^L / 16 threads; in FP32 at most 64 registers a thread, so that two
-// 512-thread blocks fit an SM.
-template <typename T, int L, int RB>
-constexpr int rows_min_blocks() {
-  return sizeof(T) == 4 ? ((1024 / (RB * (1 << L) / 16)) > 0 ? 1024 / (RB * (1 << L) / 16) : 1) : 1;
+// async 16-byte copy global -> shared (no registers), completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// stage the twiddle tables (global layout: two-level tables, then the pass tables; the
+// count padded to whole 16-byte chunks)
+template <typename T, bool INV>
+__device__ __forceinline__ void stage_twiddles_async(cpx<T>* s_tw, const cpx<T>* __restrict__ g, int L) {
+  const int chunks = (int)(tw_count<T, INV>(L) * sizeof(cpx<T>) / 16);
+  for (int i = threadIdx.x; i < chunks; i += blockDim.x)
+    cp_async16(reinterpret_cast<char*>(s_tw) + 16 * i, reinterpret_cast<const char*>(g) + 16 * i);
 }
 
-// RB rows per CTA, NT = 2^L / 16 threads per row.
+// Blocks of RB * 2^L / 16 threads; for the long FP32 rows at most 64 registers a
+// thread, so that two 512-thread blocks fit an SM.
+template <typename T, int L, int RB>
+constexpr int rows_min_blocks() {
+  return (sizeof(T) == 4 && L >= 11) ? 1024 / (RB * (1 << L) / 16) : 1;
+}
+
+// Each CTA stages the twiddles (asynchronously, overlapping its first loads), then
+// takes the work items blockIdx.x, blockIdx.x + gridDim.x, ... (the launch uses one
+// item per CTA); an item is RB consecutive rows of one (rhs, channel) grid, the row
+// groups of one grid being consecutive items.  NT = 2^L / 16 threads per row.
 template <typename T, int L, int RB>
 __global__ void __launch_bounds__(RB*(1 << L) / 16, (rows_min_blocks<T, L, RB>())) k_rows_fwd(RowsArgs<T> a) {
   constexpr int N2 = 1 << L, NT = N2 / 16, BUF = row_buf(N2);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   const int q = threadIdx.x / NT, t = threadIdx.x - q * NT;
-  const int cr = blockIdx.y;
-  const long long y0 = a.row0 + (long long)blockIdx.x * RB;
-  const long long y = y0 + q;
   cpx<T>* b = buf + q * BUF;
   cpx<T>* s_tw = buf + RB * BUF;
-  stage_twiddles(s_tw, a.tw, N2);
+  stage_twiddles_async<T, false>(s_tw, a.tw, L);
   const fft::Twiddle2<T> tw{s_tw, s_tw + tw_hi(N2)};
   const fft::Twiddle2<T> wn{s_tw + tw_hi(N2) + 64, s_tw + 2 * tw_hi(N2) + 64};
-  {
-    const T* src = a.gin + (size_t)cr * a.G + y * a.nf;
-    const bool rin = y < a.row_hi;
-    for (int i = t; i < N2; i += NT) {
-      cpx<T> v{T(0), T(0)};
-      if (rin && 2 * i + 1 >= a.col_lo && 2 * i < a.col_hi) {
-        const typename Vec2<T>::type u = *reinterpret_cast<const typename Vec2<T>::type*>(src + 2 * i);
-        v = {u.x, u.y};
-      }
-      b[fft::pad(i)] = v;  // z[i] = x[2i] + i x[2i+1]
-    }
-  }
-  __syncthreads();
-  fft_block<false, L>(b, tw, t);
-  // real split of the RB rows at m = 0..M; the RB values of one m are adjacent in X
-  cpx<T>* dst = a.X + (size_t)cr * (a.M + 1) * a.nf + y0;
-  for (int m = threadIdx.x; m <= a.M; m += blockDim.x) {
-    const cpx<T> w = wn(m);
-    cpx<T> out[RB];
+  const cpx<T>* ptab = s_tw + 2 * (tw_hi(N2) + 64);
+  bool first = true;
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int cr = (int)(item / a.npairs);
+    const long long y0 = a.row0 + (item - (long long)cr * a.npairs) * RB;
+    const long long y = y0 + q;
+    {
+      // 16 elements a thread: every load is issued before the first shared-memory store
+      const T* src = a.gin + (size_t)cr * a.G + y * a.nf;
+      const bool rin = y < a.row_hi;
+      cpx<T> v[16];
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const cpx<T>* br = buf + r * BUF;
-      out[r] = fft::r2c_split(br[fft::pad(m)], br[fft::pad((N2 - m) & (N2 - 1))], w);
+      for (int u = 0; u < 16; ++u) {
+        const int i = t + u * NT;
+        v[u] = {T(0), T(0)};
+        if (rin && 2 * i + 1 >= a.col_lo && 2 * i < a.col_hi) {
+          const typename Vec2<T>::type w = *reinterpret_cast<const typename Vec2<T>::type*>(src + 2 * i);
+          v[u] = {w.x, w.y};
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) b[fft::pad(t + u * NT)] = v[u];  // z[i] = x[2i] + i x[2i+1]
     }
-    store_rb<T, RB>(dst + (size_t)m * a.nf, out);
+    if (first) {
+      cp_async_wait_all();
+      first = false;
+    }
+    __syncthreads();
+    fft_block<false, L>(b, tw, ptab, t);
+    // real split of the RB rows at m = 0..M; the RB values of one m are adjacent in X
+    cpx<T>* dst = a.X + (size_t)cr * (a.M + 1) * a.nf + y0;
+    for (int m = threadIdx.x; m <= a.M; m += blockDim.x) {
+      const cpx<T> w = wn(m);
+      cpx<T> out[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const cpx<T>* br = buf + r * BUF;
+        out[r] = fft::r2c_split(br[fft::pad(m)], br[fft::pad((N2 - m) & (N2 - 1))], w);
+      }
+      store_rb<T, RB>(dst + (size_t)m * a.nf, out);
+    }
+    __syncthreads();  // the buffers are refilled by the next item
   }
+  if (first) cp_async_wait_all();
 }
 
 // Inverse of k_rows_fwd: modes 0..M of RB rows (zero above M; the imaginary part of
@@ -186,52 +244,75 @@ __global__ void __launch_bounds__(RB*(1 << L) / 16, (rows_min_blocks<T, L, RB>()
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   const int q = threadIdx.x / NT, t = threadIdx.x - q * NT;
-  const int cr = blockIdx.y;
-  const long long y0 = a.row0 + (long long)blockIdx.x * RB;
-  const long long y = y0 + q;
-  const cpx<T>* src = a.X + (size_t)cr * (a.M + 1) * a.nf + y0;
+  cpx<T>* b = buf + q * BUF;
   cpx<T>* s_tw = buf + RB * BUF;
-  stage_twiddles(s_tw, a.tw, N2);
+  stage_twiddles_async<T, true>(s_tw, a.tw, L);
   const fft::Twiddle2<T> tw{s_tw, s_tw + tw_hi(N2)};
   const fft::Twiddle2<T> wn{s_tw + tw_hi(N2) + 64, s_tw + 2 * tw_hi(N2) + 64};
-  for (int m = threadIdx.x; m <= N2; m += blockDim.x) {
-    cpx<T> v[RB];
-    if (m <= a.M) {
-      load_rb<T, RB>(src + (size_t)m * a.nf, v);
-    } else {
+  const cpx<T>* ptab = s_tw + 2 * (tw_hi(N2) + 64);
+  bool first = true;
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int cr = (int)(item / a.npairs);
+    const long long y0 = a.row0 + (item - (long long)cr * a.npairs) * RB;
+    const long long y = y0 + q;
+    const cpx<T>* src = a.X + (size_t)cr * (a.M + 1) * a.nf + y0;
+    {
+      // modes m = threadIdx.x + u * blockDim (U rounds cover 0..N2); loads first, then stores
+      constexpr int NTH = RB * NT, U = (N2 + 1 + NTH - 1) / NTH;
+      cpx<T> v[U][RB];
 #pragma unroll
-      for (int r = 0; r < RB; ++r) v[r] = {T(0), T(0)};
-    }
+      for (int u = 0; u < U; ++u) {
+        const int m = threadIdx.x + u * NTH;
+        if (m <= a.M) {
+          load_rb<T, RB>(src + (size_t)m * a.nf, v[u]);
+        } else {
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      if (m == 0) v[r].y = T(0);
-      buf[r * BUF + fft::pad(m)] = v[r];
-    }
-  }
-  __syncthreads();
-  // merge the pairs (k, N2 - k) in place: thread-private slots, no barrier needed inside
-  for (int kk = threadIdx.x; kk < RB * H; kk += blockDim.x) {
-    const int r = kk / H, k = kk - r * H;
-    cpx<T>* br = buf + r * BUF;
-    const cpx<T> xk = br[fft::pad(k)], xn = br[fft::pad(N2 - k)];
-    const cpx<T> zk = fft::c2r_merge(xk, xn, wn(k));
-    if (k != 0 && k != N2 / 2) br[fft::pad(N2 - k)] = fft::c2r_merge(xn, xk, wn(N2 - k));
-    br[fft::pad(k)] = zk;
-  }
-  __syncthreads();
-  cpx<T>* b = buf + q * BUF;
-  fft_block<true, L>(b, tw, t);
-  if (y < a.row_hi) {
-    T* dst = a.gout + (size_t)cr * a.G + y * a.nf;
-    for (int i = t; i < N2; i += NT) {
-      if (2 * i + 1 >= a.col_lo && 2 * i < a.col_hi) {
-        const cpx<T> v = b[fft::pad(i)];
-        *reinterpret_cast<typename Vec2<T>::type*>(dst + 2 * i) = {v.x, v.y};
+          for (int r = 0; r < RB; ++r) v[u][r] = {T(0), T(0)};
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int m = threadIdx.x + u * NTH;
+        if (m <= N2) {
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            if (m == 0) v[u][r].y = T(0);
+            buf[r * BUF + fft::pad(m)] = v[u][r];
+          }
+        }
       }
     }
+    if (first) {
+      cp_async_wait_all();
+      first = false;
+    }
+    __syncthreads();
+    // merge the pairs (k, N2 - k) in place: thread-private slots, no barrier needed inside
+    for (int kk = threadIdx.x; kk < RB * H; kk += blockDim.x) {
+      const int r = kk / H, k = kk - r * H;
+      cpx<T>* br = buf + r * BUF;
+      const cpx<T> xk = br[fft::pad(k)], xn = br[fft::pad(N2 - k)];
+      const cpx<T> zk = fft::c2r_merge(xk, xn, wn(k));
+      if (k != 0 && k != N2 / 2) br[fft::pad(N2 - k)] = fft::c2r_merge(xn, xk, wn(N2 - k));
+      br[fft::pad(k)] = zk;
+    }
+    __syncthreads();
+    fft_block<true, L>(b, tw, ptab, t);
+    if (y < a.row_hi) {
+      T* dst = a.gout + (size_t)cr * a.G + y * a.nf;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int i = t + u * NT;
+        if (2 * i + 1 >= a.col_lo && 2 * i < a.col_hi) {
+          const cpx<T> v = b[fft::pad(i)];
+          *reinterpret_cast<typename Vec2<T>::type*>(dst + 2 * i) = {v.x, v.y};
+        }
+      }
+    }
+    __syncthreads();  // the buffers are refilled by the next item
   }
+  if (first) cp_async_wait_all();
 }
-
 
 template <typename T>
 struct DiagTArgs {
@@ -319,35 +400,47 @@ constexpr int kMinLog = 4, kMaxLog = 13;       // nf = 32 .. 16384
 constexpr size_t kRowSmemMax = size_t(150) << 10;
 
 template <typename T, int L, int RB>
-void rows_launch(bool inv, const RowsArgs<T>& a, unsigned nblk, unsigned ncr, cudaStream_t st) {
-  const size_t smem = row_smem(1 << L, RB, sizeof(cpx<T>));
+void rows_launch(bool inv, const RowsArgs<T>& a, cudaStream_t st) {
+  const size_t smem = inv ? row_smem<T, true>(L, RB) : row_smem<T, false>(L, RB);
+  const int threads = RB * (1 << L) / 16;
   void (*k)(RowsArgs<T>) = inv ? k_rows_inv<T, L, RB> : k_rows_fwd<T, L, RB>;
   GPN_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k<<<dim3(nblk, ncr), RB * (1 << L) / 16, smem, st>>>(a);
+  // one item per block: adjacent row groups run together, so the two halves of a
+  // 32-byte sector of the transposed output meet in L2 (a persistent grid, tried,
+  // spread them apart and raised DRAM traffic by a quarter)
+  const long long grid = a.nitems;
+  k<<<(unsigned)grid, threads, smem, st>>>(a);
+}
+
+// RB rows per CTA where the shared memory and the block size allow it (the same
+// test as rows_per_block)
+template <typename T, int L, int RB>
+constexpr bool rows_fit() {
+  return std::max(row_smem<T, false>(L, RB), row_smem<T, true>(L, RB)) <= kRowSmemMax &&
+         RB * (1 << L) / 16 <= 1024;
 }
 
 template <typename T, int L>
-void rows_rb(bool inv, int rb, const RowsArgs<T>& a, unsigned nblk, unsigned ncr, cudaStream_t st) {
-  // two rows per CTA only where tr3_setup allows it (shared memory and block size)
-  if constexpr (row_smem(1 << L, 2, sizeof(cpx<T>)) <= kRowSmemMax && 2 * (1 << L) / 16 <= 1024) {
-    if (rb == 2) return rows_launch<T, L, 2>(inv, a, nblk, ncr, st);
+void rows_rb(bool inv, int rb, const RowsArgs<T>& a, cudaStream_t st) {
+  if constexpr (rows_fit<T, L, 2>()) {
+    if (rb == 2) return rows_launch<T, L, 2>(inv, a, st);
   }
-  rows_launch<T, L, 1>(inv, a, nblk, ncr, st);
+  rows_launch<T, L, 1>(inv, a, st);
 }
 
 template <typename T>
-void rows(bool inv, int L, int rb, const RowsArgs<T>& a, unsigned nblk, unsigned ncr, cudaStream_t st) {
+void rows(bool inv, int L, int rb, const RowsArgs<T>& a, cudaStream_t st) {
   switch (L) {
-    case 4: rows_rb<T, 4>(inv, rb, a, nblk, ncr, st); break;
-    case 5: rows_rb<T, 5>(inv, rb, a, nblk, ncr, st); break;
-    case 6: rows_rb<T, 6>(inv, rb, a, nblk, ncr, st); break;
-    case 7: rows_rb<T, 7>(inv, rb, a, nblk, ncr, st); break;
-    case 8: rows_rb<T, 8>(inv, rb, a, nblk, ncr, st); break;
-    case 9: rows_rb<T, 9>(inv, rb, a, nblk, ncr, st); break;
-    case 10: rows_rb<T, 10>(inv, rb, a, nblk, ncr, st); break;
-    case 11: rows_rb<T, 11>(inv, rb, a, nblk, ncr, st); break;
-    case 12: rows_rb<T, 12>(inv, rb, a, nblk, ncr, st); break;
-    default: rows_rb<T, 13>(inv, rb, a, nblk, ncr, st);
+    case 4: rows_rb<T, 4>(inv, rb, a, st); break;
+    case 5: rows_rb<T, 5>(inv, rb, a, st); break;
+    case 6: rows_rb<T, 6>(inv, rb, a, st); break;
+    case 7: rows_rb<T, 7>(inv, rb, a, st); break;
+    case 8: rows_rb<T, 8>(inv, rb, a, st); break;
+    case 9: rows_rb<T, 9>(inv, rb, a, st); break;
+    case 10: rows_rb<T, 10>(inv, rb, a, st); break;
+    case 11: rows_rb<T, 11>(inv, rb, a, st); break;
+    case 12: rows_rb<T, 12>(inv, rb, a, st); break;
+    default: rows_rb<T, 13>(inv, rb, a, st);
   }
 }
 
@@ -376,10 +469,11 @@ RowsArgs<T> rows_args(Plan& plan, const void* X) {
 
 template <typename T>
 void rows_run(Plan& plan, bool inv, const void* X, int R, cudaStream_t st) {
-  const RowsArgs<T> a = rows_args<T>(plan, X);
+  RowsArgs<T> a = rows_args<T>(plan, X);
   if (plan.row_hi <= a.row0) return;
-  const unsigned nblk = (unsigned)((plan.row_hi - a.row0 + plan.t3_rb - 1) / plan.t3_rb);
-  rows<T>(inv, log2_exact(plan.geom.nf / 2), plan.t3_rb, a, nblk, (unsigned)(plan.geom.C * R), st);
+  a.npairs = (plan.row_hi - a.row0 + plan.t3_rb - 1) / plan.t3_rb;
+  a.nitems = a.npairs * plan.geom.C * R;
+  rows<T>(inv, log2_exact(plan.geom.nf / 2), plan.t3_rb, a, st);
   GPN_CUDA(cudaGetLastError());
 }
 
@@ -395,14 +489,14 @@ bool tr3_supported(int d, long long nf, size_t rs) {
   if (d != 2) return false;
   const int L = log2_exact(nf / 2);
   if (nf % 2 || L < kMinLog || L > kMaxLog) return false;
-  return row_smem(1 << L, 1, 2 * rs) <= kRowSmemMax;
+  return (rs == 4 ? row_smem<float, false>(L, 1) : row_smem<double, false>(L, 1)) <= kRowSmemMax;
 }
 
 void tr3_setup(Plan& plan) {
   const long long nf = plan.geom.nf, N2 = nf / 2;
   const int L = log2_exact(N2);
-  const size_t cs = 2 * plan.real_size;
-  plan.t3_rb = (row_smem(1 << L, 2, cs) <= kRowSmemMax && 2 * (N2 / 16) <= 1024) ? 2 : 1;
+  const size_t sm2 = plan.precision == GP_FP32 ? row_smem<float, false>(L, 2) : row_smem<double, false>(L, 2);
+  plan.t3_rb = (sm2 <= kRowSmemMax && 2 * (N2 / 16) <= 1024) ? 2 : 1;
   // two-level tables, computed in float64: W_{N2}^{64 q} (q < H), W_{N2}^j (j < 64),
   // W_nf^{64 q} (q < H), W_nf^j (j < 64), with H = N2 / 64 + 1
   const int H = tw_hi((int)N2);
@@ -417,6 +511,12 @@ void tr3_setup(Plan& plan) {
   for (int j = 0; j < 64; ++j) put(j, N2);
   for (int q = 0; q < H; ++q) put(64ll * q, nf);
   for (int j = 0; j < 64; ++j) put(j, nf);
+  if (plan.precision == GP_FP32) {
+    const std::vector<double> pt = fft::pass_tables(L);
+    w.insert(w.end(), pt.begin(), pt.end());
+  }
+  const size_t count = plan.precision == GP_FP32 ? tw_count<float, false>(L) : tw_count<double, false>(L);
+  w.resize(2 * count, 0.0);  // padded to whole 16-byte chunks
   plan.tw_half = plan.alloc(w.size() * plan.real_size);
   if (plan.precision == GP_FP32) {
     std::vector<float> f(w.begin(), w.end());

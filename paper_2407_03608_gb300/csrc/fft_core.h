@@ -7,13 +7,18 @@
 // nothing is normalised (the same as cuFFT).
 #pragma once
 
+#include <cmath>
+#include <vector>
+
 namespace gpn {
 namespace fft {
 
 #ifdef __CUDACC__
 #define GPN_HD __host__ __device__ __forceinline__
+#define GPN_HDC __host__ __device__ constexpr
 #else
 #define GPN_HD inline
+#define GPN_HDC constexpr
 #endif
 
 template <typename T>
@@ -145,7 +150,8 @@ GPN_HD int pad(int i) { return i + (i >> 4); }
 // order.  A thread handles NB butterflies j = t + b * nthreads.  The pass is split
 // in a load and a store half because the transform is done in place: all loads of a
 // pass must precede its stores (a block barrier in between on the device).
-// tw(i) returns W_N^i = e^{-2 pi i i / N}, 0 <= i < N.
+// tw(r, k, i) returns the twiddle of input r of a butterfly with k = j mod Ns, which is
+// W_N^i with i = r k N / (Ns R) (0 <= i < N).
 template <int R, int NB, typename T>
 struct Pass {
   cpx<T> v[NB][R];
@@ -169,7 +175,7 @@ struct Pass {
         const int step = k * (N / (Ns * R));
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          cpx<T> w = tw(r * step);
+          cpx<T> w = tw(r, k, r * step);
           if (INV) w.y = -w.y;
           v[b][r] = cmul(v[b][r], w);
         }
@@ -190,6 +196,47 @@ struct Twiddle2 {
   const cpx<T>* hi;
   const cpx<T>* lo;
   GPN_HD cpx<T> operator()(int i) const { return cmul(hi[i >> 6], lo[i & 63]); }
+  GPN_HD cpx<T> operator()(int, int, int i) const { return (*this)(i); }
+};
+
+// The radix-16 passes of a length-N FFT in the device kernels' order: one pass of radix
+// 2^(L mod 4) at span 1 when L = log2 N is not a multiple of 4, then radix-16 passes at
+// spans s0, 16 s0, ... (s0 = 2^(L mod 4)).  A radix-16 pass at span Ns > 1 needs the
+// 15 Ns twiddles W_{16 Ns}^{r k} (r = 1..15, k < Ns); pass_table lays them out as
+// [r - 1][k] (consecutive k for consecutive threads) and concatenates the passes.
+GPN_HDC int first_span(int L) { return 1 << (L % 4); }
+// offset of the table of the radix-16 pass at span Ns (a power of two >= first_span)
+GPN_HDC int pass_table_offset(int L, int Ns) {
+  int off = 0;
+  for (int s = first_span(L); s < Ns; s *= 16)
+    if (s > 1) off += 15 * s;
+  return off;
+}
+GPN_HDC int pass_table_size(int L) { return pass_table_offset(L, 1 << L); }
+
+// Host: the concatenated pass tables of a length-2^L FFT as interleaved (re, im)
+// float64 values, computed from the angle 2 pi r k / (16 Ns) directly.
+inline std::vector<double> pass_tables(int L) {
+  std::vector<double> t(2 * (size_t)pass_table_size(L));
+  for (int s = first_span(L); s < (1 << L); s *= 16) {
+    if (s == 1) continue;
+    const int off = pass_table_offset(L, s);
+    for (int r = 1; r < 16; ++r)
+      for (int k = 0; k < s; ++k) {
+        const double th = 2.0 * 3.14159265358979323846264338327950288 * (double)(r * k) / (16.0 * s);
+        t[2 * ((size_t)off + (r - 1) * s + k)] = std::cos(th);
+        t[2 * ((size_t)off + (r - 1) * s + k) + 1] = -std::sin(th);
+      }
+  }
+  return t;
+}
+
+// twiddle functor of one radix-16 pass over its table in consumption order
+template <typename T>
+struct PassTwiddle {
+  const cpx<T>* tab;  // [15][Ns]
+  int Ns;
+  GPN_HD cpx<T> operator()(int r, int k, int) const { return tab[(r - 1) * Ns + k]; }
 };
 
 // Real-input split (forward): z[n] = x[2n] + i x[2n+1] with Z = FFT_{N2}(z).  The

@@ -19,33 +19,44 @@ using gpn::fft::cpx;
 using gpn::fft::Pass;
 using C = cpx<double>;
 
+// a pass with the two-level twiddle (the real split's functor), for the radix-2/4/8 pass
 template <int R, int NB, bool INV>
-void pass(std::vector<C>& buf, const std::vector<C>& tw, int N, int Ns) {
+void pass2(std::vector<C>& buf, int N, int Ns) {
   const int nt = N / 16;
   std::vector<Pass<R, NB, double>> st(nt);
   for (int t = 0; t < nt; ++t) st[t].load(buf.data(), N, t, nt);
-  // the two-level twiddle of the device kernels
   std::vector<C> hi(N / 64 + 1), lo(64);
-  for (int q = 0; q < (int)hi.size(); ++q) hi[q] = tw[(64 * q) % N];
+  for (int q = 0; q < (int)hi.size(); ++q) hi[q] = {std::cos(2 * M_PI * (64.0 * q) / N), -std::sin(2 * M_PI * (64.0 * q) / N)};
   for (int j = 0; j < 64; ++j) lo[j] = {std::cos(2 * M_PI * j / N), -std::sin(2 * M_PI * j / N)};
   const gpn::fft::Twiddle2<double> t2{hi.data(), lo.data()};
   for (int t = 0; t < nt; ++t) st[t].template store<INV>(buf.data(), t2, N, Ns, t, nt);
 }
 
+// a radix-16 pass with its table from gpn::fft::pass_tables, as on the device
+template <bool INV>
+void pass16(std::vector<C>& buf, const std::vector<C>& tab, int L, int Ns) {
+  const int N = 1 << L, nt = N / 16;
+  std::vector<Pass<16, 1, double>> st(nt);
+  for (int t = 0; t < nt; ++t) st[t].load(buf.data(), N, t, nt);
+  const gpn::fft::PassTwiddle<double> tw{tab.data() + gpn::fft::pass_table_offset(L, Ns), Ns};
+  for (int t = 0; t < nt; ++t) st[t].template store<INV>(buf.data(), tw, N, Ns, t, nt);
+}
+
 template <bool INV>
 void fft(std::vector<C>& buf, int L) {
   const int N = 1 << L;
-  std::vector<C> tw(N);
-  for (int i = 0; i < N; ++i) tw[i] = {std::cos(2 * M_PI * i / N), -std::sin(2 * M_PI * i / N)};
+  const std::vector<double> raw = gpn::fft::pass_tables(L);
+  std::vector<C> tab(raw.size() / 2 + 1);
+  for (size_t i = 0; i < raw.size() / 2; ++i) tab[i] = {raw[2 * i], raw[2 * i + 1]};
   int Ns = 1;
   switch (L % 4) {
-    case 1: pass<2, 8, INV>(buf, tw, N, Ns); Ns *= 2; break;
-    case 2: pass<4, 4, INV>(buf, tw, N, Ns); Ns *= 4; break;
-    case 3: pass<8, 2, INV>(buf, tw, N, Ns); Ns *= 8; break;
+    case 1: pass2<2, 8, INV>(buf, N, Ns); Ns *= 2; break;
+    case 2: pass2<4, 4, INV>(buf, N, Ns); Ns *= 4; break;
+    case 3: pass2<8, 2, INV>(buf, N, Ns); Ns *= 8; break;
     default: break;
   }
   for (int q = 0; q < L / 4; ++q) {
-    pass<16, 1, INV>(buf, tw, N, Ns);
+    pass16<INV>(buf, tab, L, Ns);
     Ns *= 16;
   }
 }
