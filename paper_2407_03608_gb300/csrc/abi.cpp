@@ -78,22 +78,27 @@ void* tmp_alloc_cb(void* ctx, size_t bytes) {
 }
 
 // Spread/interp tile edge: the largest candidate whose shared tile fits the budget
-// (64 KB keeps several CTAs per SM) and that covers a point's support in two
-// bins (tile >= width - 1).
+// (64 KB keeps several CTAs per SM, then the spreading maximum) with all channels, and
+// that covers a point's support in two bins (tile >= width - 1).  When no tile holds
+// every channel, the largest holding one channel: the spreading then runs in channel
+// chunks.
 int choose_tile(int d, int C, size_t rs, int width) {
   static const int c1[] = {4096, 2048, 1024, 512, 256, 128, 64, 32, 16};
   static const int c2[] = {64, 48, 32, 24, 16, 12, 8};
   static const int c3[] = {16, 12, 10, 8, 6, 4};
   const int* c = d == 1 ? c1 : (d == 2 ? c2 : c3);
   int nc = d == 1 ? 9 : (d == 2 ? 7 : 6);
-  for (size_t budget : {size_t(64) << 10, size_t(160) << 10}) {
-    for (int i = 0; i < nc; ++i) {
-      if (c[i] < width - 1) continue;
-      if (spread_smem_bytes(d, c[i], C, rs, width) <= budget && interp_stage_bytes(d, c[i], width, rs) <= kInterpSmemMax)
-        return c[i];
+  for (int chans : {C, 1}) {
+    for (size_t budget : {size_t(64) << 10, kSpreadSmemMax}) {
+      for (int i = 0; i < nc; ++i) {
+        if (c[i] < width - 1) continue;
+        if (spread_smem_bytes(d, c[i], chans, rs, width) <= budget &&
+            interp_stage_bytes(d, c[i], width, rs) <= kInterpSmemMax)
+          return c[i];
+      }
     }
   }
-  fail(GP_EUNSUPPORTED, "no spreading tile fits in shared memory for these channels and kernel width");
+  fail(GP_EUNSUPPORTED, "no spreading tile fits in shared memory for this kernel width");
 }
 
 int set_error(const Error& e) {

@@ -46,7 +46,8 @@ struct SpreadArgs {
   T inv_halfw;
   int tile;
   int pitch;             // padded extent of the last tile dimension in shared memory
-  int C;
+  int C;                 // channels of one chunk (blockIdx.z = chunk)
+  int Ctot;              // channels in total
   unsigned pmagic;       // ceil(2^24 / P): (g * pmagic) >> 24 == g / P for g < 2^24 / P
   unsigned wmagic;       // ceil(2^12 / width): (x * wmagic) >> 12 == x / width for x < 256
 };
@@ -83,7 +84,8 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_count[2];
   __shared__ float s_red[8];
-  const int TS = a.tile, TP = a.pitch, W = a.width, C = a.C;
+  const int ch0 = blockIdx.z * a.C;                 // first channel of this chunk
+  const int TS = a.tile, TP = a.pitch, W = a.width, C = min(a.C, a.Ctot - ch0);
   int lead = 1;  // cells in the leading D-1 dimensions
 #pragma unroll
   for (int q = 0; q < D - 1; ++q) lead *= TS;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
         for (int j = 0; j < W; ++j) psi[q * W + j] = es_psi<T>((T)j - xq, a.beta, a.inv_halfw);
       }
       const T amp = (T)alpha_r[p] * scale;
-      const T* wkp = a.wk + (size_t)p * C;
+      const T* wkp = a.wk + (size_t)p * a.Ctot + ch0;
 #pragma unroll
       for (int k = 0; k < CMAX; ++k)
         if (k < C) s_wk[k * kBatch + slot] = wkp[k] * amp;
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs<T> a) {
       sstride *= (q == D - 1) ? TP : TS;
     }
     if (!in) continue;
-    T* dst = a.grid + (size_t)r * C * a.G + gidx;
+    T* dst = a.grid + ((size_t)r * a.Ctot + ch0) * a.G + gidx;
 #pragma unroll
     for (int k = 0; k < CMAX; ++k) {
       if (k < C) {
@@ -334,15 +336,21 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
   a.inv_halfw = (T)(2.0 / g.width);
   a.tile = g.tile;
   a.pitch = spread_pitch(g.d, g.tile);
-  a.C = g.C;
+  // channels per launch chunk: all of them when the shared tile fits, else fewer
+  int cc = g.C;
+  while (cc > 1 && spread_smem_bytes(g.d, g.tile, cc, sizeof(T), g.width) > kSpreadSmemMax) --cc;
+  GPN_CHECK(spread_smem_bytes(g.d, g.tile, cc, sizeof(T), g.width) <= kSpreadSmemMax, GP_EUNSUPPORTED,
+            "spreading tile does not fit in shared memory");
+  a.C = cc;
+  a.Ctot = g.C;
   {
     unsigned P = 1;
     for (int q = 0; q < g.d - 1; ++q) P *= (unsigned)g.width;
     a.pmagic = (unsigned)(((1ull << 24) + P - 1) / P);
     a.wmagic = (unsigned)(((1u << 12) + g.width - 1) / g.width);
   }
-  size_t smem = spread_smem_bytes(g.d, g.tile, g.C, sizeof(T), g.width);
-  dim3 grid((unsigned)plan.n_active_tiles, (unsigned)R);
+  size_t smem = spread_smem_bytes(g.d, g.tile, cc, sizeof(T), g.width);
+  dim3 grid((unsigned)plan.n_active_tiles, (unsigned)R, (unsigned)((g.C + cc - 1) / cc));
   switch (g.d) {
     case 1: launch_c<T, 1>(a, grid, smem, st); break;
     case 2: launch_c<T, 2>(a, grid, smem, st); break;

@@ -1,0 +1,180 @@
+"""Request loop for GP solves of uneven size, dimension and hyperparameters.
+
+Each request is a GP regression problem (points, scale fields s and l, smoothness nu,
+noise eta, right-hand sides y).  The server takes the requests in arrival order on one
+GPU and, for each one:
+
+1. admits it by device-memory footprint: the plan is built at the target eps when its
+   resident bytes fit the HBM budget, else at the next coarser eps (1e-5, 1e-4, ...),
+   and the eps used is recorded;
+2. builds the plans (FP32 for the inner CG, FP64 for the residuals of the iterative
+   refinement; both hold the sorted points, Chebyshev weights, A' and grids resident
+   on the device for the whole solve);
+3. solves (K~ + eta^2 I) alpha = y for all right-hand sides at once with
+   ``gp_cg_solve_refined`` and copies alpha back to the host;
+4. frees the plans.
+
+Latency is measured per request as finish - arrival on a replayed clock: a request
+starts when it has arrived and the previous one has finished, and its service time is
+the measured wall time of steps 1-4 (host-synchronised).  The arrival times are
+rescaled so that the offered load is a chosen fraction of the measured capacity,
+which gives p50/p99 latency at that load without idling the GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+EPS_LADDER = (1e-6, 1e-5, 1e-4, 1e-3)
+
+
+@dataclass
+class Served:
+    rid: int
+    n: int
+    d: int
+    nu: float
+    r: int
+    eps: float
+    service_s: float
+    plan_s: float
+    solve_s: float
+    iters: int
+    relres: float
+    bytes_resident: int
+
+
+def _rhs(req) -> int:
+    y = np.asarray(req.y)
+    return 1 if y.ndim == 1 else int(y.shape[1])
+
+
+def _plan_fitting(gpn, req, budget: int, eps_target: float, precision, extra: Optional[dict] = None):
+    """The plan at the finest eps of the ladder (from eps_target) whose footprint fits."""
+    last = None
+    for eps in [e for e in EPS_LADDER if e >= eps_target * (1 - 1e-12)]:
+        try:
+            kw = dict(extra or {})
+            return gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=precision,
+                            max_rhs=_rhs(req), max_bytes=int(budget), **kw), eps
+        except gpn.GPError as e:
+            if e.status != gpn.abi.GP_ENOMEM:
+                raise
+            last = e
+    raise last
+
+
+class Server:
+    """Serves requests one after another on the current CUDA device."""
+
+    def __init__(self, hbm_budget: float = 120e9, eps_target: float = 1e-6, rtol: float = 1e-8,
+                 inner_rtol: float = 1e-4, maxit: int = 20000, outer_max: int = 20):
+        import paper_2407_03608_gb300 as gpn
+        self.gpn = gpn
+        self.budget = int(hbm_budget)
+        self.eps_target = eps_target
+        self.rtol = rtol
+        self.inner_rtol = inner_rtol
+        self.maxit = maxit
+        self.outer_max = outer_max
+
+    def serve_one(self, req) -> Served:
+        import torch
+        gpn = self.gpn
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hi, eps = _plan_fitting(gpn, req, self.budget // 2, self.eps_target, gpn.GP_FP64)
+        lo = None
+        try:
+            lo = gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=gpn.GP_FP32,
+                          max_rhs=_rhs(req), **hi.matched_opts())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            y = np.asarray(req.y, dtype=np.float64)
+            alpha, info = hi.solve_refined(lo, y, req.eta ** 2, rtol=self.rtol, inner_rtol=self.inner_rtol,
+                                           outer_max=self.outer_max, maxit=self.maxit)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            iters = int(np.max(info["iters"]))
+            relres = float(np.max(info["relres"]))
+            nbytes = int(hi.info["bytes_resident"] + lo.info["bytes_resident"])
+        finally:
+            if lo is not None:
+                lo.close()
+            hi.close()
+        return Served(req.rid, req.points.shape[0], req.points.shape[1], req.nu, _rhs(req), eps, t2 - t0, t1 - t0,
+                      t2 - t1, iters, relres, nbytes)
+
+    def serve(self, requests, load: float = 0.8) -> dict:
+        """Serve all requests; latency statistics at `load` times the measured capacity."""
+        done: List[Served] = [self.serve_one(r) for r in requests]
+        service = np.array([s.service_s for s in done])
+        arrivals = np.array([r.arrival_s for r in requests])
+        lat, rate = replay_latency(arrivals, service, load)
+        return {
+            "requests": len(done),
+            "load": load,
+            "offered_rate_per_s": rate,
+            "capacity_solves_per_s": 1.0 / float(np.mean(service)),
+            "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)),
+            "service_p50_s": float(np.percentile(service, 50)),
+            "service_p99_s": float(np.percentile(service, 99)),
+            "plan_share": float(np.sum([s.plan_s for s in done]) / np.sum(service)),
+            "eps_used": {str(e): int(sum(1 for s in done if s.eps == e)) for e in sorted({s.eps for s in done})},
+            "max_relres": float(max(s.relres for s in done)),
+            "max_iters": int(max(s.iters for s in done)),
+            "points_total": int(sum(s.n * s.r for s in done)),
+            "records": [s.__dict__ for s in done],
+        }
+
+
+def replay_latency(arrivals, service, load: float):
+    """Latency (finish - arrival) of FIFO service on one server when the arrival times
+    are rescaled to an offered rate of load / mean(service).  Returns (latency, rate)."""
+    arrivals = np.asarray(arrivals, dtype=np.float64)
+    service = np.asarray(service, dtype=np.float64)
+    span = arrivals[-1] - arrivals[0] if len(arrivals) > 1 else 0.0
+    rate0 = (len(arrivals) - 1) / span if span > 0 else 1.0
+    rate = load / float(np.mean(service))
+    arr = (arrivals - arrivals[0]) * (rate0 / rate)
+    finish = np.empty_like(arr)
+    free_at = -np.inf
+    for i, (a, s) in enumerate(zip(arr, service)):
+        start = max(a, free_at)
+        free_at = start + s
+        finish[i] = free_at
+    return finish - arr, rate
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--n-min", type=float, default=1e3)
+    ap.add_argument("--n-max", type=float, default=1e6)
+    ap.add_argument("--max-rhs", type=int, default=16)
+    ap.add_argument("--dims", default="1,2,3")
+    ap.add_argument("--nus", default="0.5,1.5,2.5")
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--seed", type=int, default=100)
+    ap.add_argument("--records", action="store_true", help="include per-request records")
+    args = ap.parse_args()
+    import gpinputs
+    reqs = gpinputs.serving_stream(args.requests, n_min=int(args.n_min), n_max=int(args.n_max), seed=args.seed,
+                                   max_rhs=args.max_rhs, dims=tuple(int(v) for v in args.dims.split(",")),
+                                   nus=tuple(float(v) for v in args.nus.split(",")))
+    out = Server(hbm_budget=args.budget_gb * 1e9, eps_target=args.eps).serve(reqs, load=args.load)
+    if not args.records:
+        out.pop("records")
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -146,3 +146,20 @@ def test_config1_matvec_vs_dense_K(gpn):
     p32 = gpn.Plan(w.points, w.s, w.l, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32)
     e32 = rel(p32.matvec(w.alpha), K @ w.alpha)
     assert e32 <= 1e-4, e32
+
+
+def test_3d_many_channels_spreads_in_chunks(gpn):
+    """d=3 with 25 channels and a wide FP64 kernel: no tile holds every channel in
+    shared memory, so the spreading runs in channel chunks; parity vs the exact NUDFT."""
+    w = gpinputs.config_3d(200)
+    X = w.points
+    wp, sig = okern.paper_fields(w.s, w.l, 3)
+    p = explicit_params(3, 2.5, sig, X, n_t=10, n_sigma=24, M=8)
+    plan = gpn.Plan(X, w.s, w.l, nu=2.5, eps=1e-6, precision=gpn.GP_FP64, nufft_tol=1e-11, **plan_kwargs(p))
+    C = p.n_sigma + 1
+    W = plan.info["kernel_width"]
+    assert plan.info["tile"] ** 3 * C * 8 > 160 * 1024, (plan.info["tile"], W)   # a full tile cannot fit
+    alpha = gpinputs.random_alpha(200, 1, seed=13)
+    ref = ktilde.matvec(X, wp, sig, alpha, p)
+    got = plan.matvec(torch.from_numpy(alpha).cuda()).cpu().numpy()
+    assert rel(got, ref) <= 1e-9
