@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the side measurements (config 1 latency, batched R, config 3, served solves)")
+    ap.add_argument("--serve-requests", type=int, default=16)
     return ap.parse_args()
 
 
@@ -345,6 +348,115 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ side measurements
+def _events_ms(fn, reps):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_config1(dev):
+    """d=1, N=2000, Matern 3/2, eps=1e-6 (latency-bound): one matvec and a CG solve to 1e-8, FP64."""
+    import torch
+    import gpinputs
+    import paper_2407_03608_gb300 as gpn
+    from paper_2407_03608_gb300 import abi
+    w = gpinputs.config_1d()
+    plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
+                    torch.from_numpy(w.l).to(dev), nu=w.nu, eps=w.eps, precision=gpn.GP_FP64)
+    a = torch.from_numpy(w.alpha).to(dev)
+    out = torch.empty_like(a)
+    for _ in range(5):
+        abi.gp_matvec(plan.handle, a, out, 1, 0.0)
+    mv_ms = _events_ms(lambda: abi.gp_matvec(plan.handle, a, out, 1, 0.0), 50)
+    y = torch.from_numpy(w.y).to(dev)
+    x = torch.empty_like(y)
+    its = []
+    solve_ms = _events_ms(lambda: its.append(abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-8, 20000)[1][0]), 3)
+    plan.close()
+    return {"workload": w.name, "precision": "fp64", "matvec_us": round(mv_ms * 1e3, 2),
+            "cg_solve_ms": round(solve_ms, 3), "cg_iters": int(its[-1]), "rtol": 1e-8}
+
+
+def measure_batched(dev, n, R=8, steps=3):
+    """The 2-D clustered workload with R right-hand sides per CG iteration (8 noisy y vectors)."""
+    import torch
+    import gpinputs
+    import paper_2407_03608_gb300 as gpn
+    from paper_2407_03608_gb300 import abi
+    w = gpinputs.config_2d(n, 1.5)
+    plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
+                    torch.from_numpy(w.l).to(dev), nu=1.5, eps=1e-6, precision=gpn.GP_FP32, max_rhs=R)
+    rng = np.random.default_rng(10)
+    Y = torch.from_numpy(np.ascontiguousarray(
+        (w.y[:, None] + 0.05 * rng.standard_normal((w.N, R))).T)).to(dev)   # (R, N) = column-major N x R
+    X = torch.empty_like(Y)
+    abi.gp_cg_solve(plan.handle, Y, X, R, w.eta ** 2, 1e-30, 2)
+    ms = _events_ms(lambda: abi.gp_cg_solve(plan.handle, Y, X, R, w.eta ** 2, 1e-30, steps), 1) / steps
+    nbytes = plan.info["bytes_resident"]
+    plan.close()
+    return {"workload": w.name, "R": R, "precision": "fp32 (f64 CG)", "ms_per_step": round(ms, 3),
+            "value": round(w.N * R / (ms * 1e-3) / 1e6, 3), "unit": "Mpts/s (N*R per CG iteration)",
+            "bytes_resident": int(nbytes)}
+
+
+def measure_config3(dev, steps=3):
+    """d=3, N=2e6 uniform, Matern 5/2, eps=1e-6, FP32: one CG iteration."""
+    import torch
+    import gpinputs
+    import paper_2407_03608_gb300 as gpn
+    from paper_2407_03608_gb300 import abi
+    w = gpinputs.config_3d()
+    t0 = time.perf_counter()
+    plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
+                    torch.from_numpy(w.l).to(dev), nu=w.nu, eps=w.eps, precision=gpn.GP_FP32)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    y = torch.from_numpy(w.y).to(dev)
+    x = torch.empty_like(y)
+    abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, 1)
+    ms = _events_ms(lambda: abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, steps), 1) / steps
+    i = plan.info
+    plan.close()
+    return {"workload": w.name, "precision": "fp32 (f64 CG)", "ms_per_step": round(ms, 3),
+            "value": round(w.N / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "plan_seconds": round(plan_s, 3),
+            "nf": i["nf"], "M": i["M"], "n_sigma": i["n_sigma"], "kernel_width": i["kernel_width"],
+            "bytes_resident": int(i["bytes_resident"])}
+
+
+def measure_serving(n_requests):
+    """A bounded sample of the serving stream: solves to rtol 1e-8 (FP32 CG inside FP64
+    refinement), p50/p99 latency at 80% of the measured capacity."""
+    import gpinputs
+    from paper_2407_03608_gb300.serving import Server
+    reqs = gpinputs.serving_stream(n_requests, n_min=1000, n_max=50_000, dims=(1, 2), nus=(1.5, 2.5), max_rhs=4)
+    out = Server(hbm_budget=120e9, eps_target=1e-6).serve(reqs, load=0.8)
+    out.pop("records")
+    out["sample"] = ("%d requests of the serving stream (seed 100): N log-uniform in [1e3, 5e4], d in {1, 2}, "
+                     "nu in {3/2, 5/2}, R in 1..4" % n_requests)
+    return out
+
+
+def side_measurements(args, dev):
+    res = {}
+    for name, fn in (("config1", lambda: measure_config1(dev)),
+                     ("batched", lambda: measure_batched(dev, args.n)),
+                     ("config3", lambda: measure_config3(dev)),
+                     ("served", lambda: measure_serving(args.serve_requests))):
+        try:
+            res[name] = fn()
+        except Exception as e:  # recorded, not fatal: the headline line is still printed
+            res[name] = {"error": "%s: %s" % (type(e).__name__, str(e)[:200])}
+    return res
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -352,11 +464,14 @@ def main():
         run_reference(args, ws, rank)
         return
     result, w, out_sample, plan = run_ours(args, ws, rank, local)
+    plan.close()
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(w, out_sample, args.cpu_seconds)
+        if ws == 1 and not args.no_extras:
+            import torch
+            result["side"] = side_measurements(args, torch.device("cuda", local))
         print(json.dumps(result), flush=True)
-    plan.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

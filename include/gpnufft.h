@@ -75,7 +75,7 @@ enum {
   GP_SET_NUFFT = 1u << 5,     /* nufft_tol, upsampfac        (App. D)                */
   GP_SET_BOX = 1u << 6,       /* box_lo, box_hi: region all points and queries lie in */
   GP_SET_NF = 1u << 7,        /* nf: fine-grid size per dimension (FFT length)        */
-  GP_SET_TILE = 1u << 8       /* tile: spread/interp tile edge in fine-grid cells     */
+  GP_SET_TILE = 1u << 8       /* tile: spread/interp tile edge in fine-grid cells; for d >= 2 a multiple of 4 (FP32) or 2 (FP64) */
 };
 
 typedef struct gp_plan_opts {

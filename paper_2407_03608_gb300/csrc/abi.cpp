@@ -77,7 +77,8 @@ void* tmp_alloc_cb(void* ctx, size_t bytes) {
   return p;
 }
 
-// Spread/interp tile edge: the largest candidate whose shared tile fits the budget
+// Spread/interp tile edge (with d >= 2, a multiple of 16 bytes of grid values): the
+// largest candidate whose shared tile fits the budget
 // (64 KB keeps several CTAs per SM, then the spreading maximum) with all channels, and
 // that covers a point's support in two bins (tile >= width - 1).  When no tile holds
 // every channel, the largest holding one channel: the spreading then runs in channel
@@ -92,6 +93,9 @@ int choose_tile(int d, int C, size_t rs, int width) {
     for (size_t budget : {size_t(64) << 10, kSpreadSmemMax}) {
       for (int i = 0; i < nc; ++i) {
         if (c[i] < width - 1) continue;
+        // d >= 2 stages interp tiles with TMA from x = bin * tile: 16-byte aligned only
+        // when tile * rs is a multiple of 16
+        if (d >= 2 && (c[i] * rs) % 16 != 0) continue;
         if (spread_smem_bytes(d, c[i], chans, rs, width) <= budget &&
             interp_stage_bytes(d, c[i], width, rs) <= kInterpSmemMax)
           return c[i];
@@ -333,6 +337,8 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   select_hyper(h, o, o.precision, N);
   const int C = h.n_sigma + 1;
   h.tile = (o.set & GP_SET_TILE) ? o.tile : choose_tile(d, C, plan->real_size, h.width);
+  GPN_CHECK(d == 1 || (h.tile * plan->real_size) % 16 == 0, GP_EINVAL,
+            "tile must be a multiple of 16 bytes of grid values (4 in FP32, 2 in FP64) for d >= 2");
   GPN_CHECK(h.tile >= h.width - 1 && h.tile >= 1, GP_EINVAL, "tile must be >= kernel width - 1");
   build_tables(h, plan->tb);
 

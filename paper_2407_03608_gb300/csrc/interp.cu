@@ -280,6 +280,9 @@ void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, dou
   a.shift = shift;
   a.out = out_sorted;
   a.status = plan.dev_status;
+  // a TMA tile copy must start on a 16-byte boundary along x (x = bin * tile)
+  GPN_CHECK(g.d == 1 || (g.tile * sizeof(T)) % 16 == 0, GP_EUNSUPPORTED,
+            "interp tile must be a multiple of 16 bytes of grid values for the TMA copies");
   const size_t smem = 128 + (size_t)a.box_bytes;
   dim3 grid((unsigned)ps.n_active_bins, (unsigned)R);
   switch (g.d) {
