@@ -146,6 +146,8 @@ Plan::~Plan() {
   for (auto& kv : fft_inv) cufftDestroy(kv.second);
   for (auto& kv : fft_col) cufftDestroy(kv.second);
   for (auto& kv : fft_t3) cufftDestroy(kv.second);
+  if (cg_graph.exec) cudaGraphExecDestroy(cg_graph.exec);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   for (void* p : owned) cudaFree(p);
   if (host_scal) cudaFreeHost(host_scal);
   if (host_status) cudaFreeHost(host_status);
@@ -425,6 +427,7 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->stage_in = (double*)plan->alloc(vb);
   plan->stage_out = (double*)plan->alloc(vb);
   plan->scal = (double*)plan->alloc(sizeof(double) * 8 * max_rhs);
+  plan->cg_cnt = (int*)plan->alloc(sizeof(int) * (max_rhs + 1));
   plan->partials = (double*)plan->alloc(sizeof(double) * 512 * max_rhs);
   GPN_CUDA(cudaMallocHost(&plan->host_scal, sizeof(double) * 8 * max_rhs));
   if (plan->tr3) {

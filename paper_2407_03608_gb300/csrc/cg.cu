@@ -6,6 +6,9 @@
 //
 // Device scalars (plan.scal), per column r of R:
 //   [0] rr = ||r||^2   [1] pAp   [2] rr_new   [3] yy = ||y||^2   [4] active (1/0)
+// Convergence and breakdown are decided on the device at the end of every iteration
+// (k_cg_check), so the host runs blocks of iterations and looks at the flags once per
+// block; a full block is replayed from a CUDA graph captured once per solve.
 #include <cmath>
 #include <vector>
 
@@ -101,6 +104,22 @@ __global__ void k_roll_scalars(double* scal, int R) {
   if (r < R && scal[4 * R + r] != 0.0) scal[0 * R + r] = scal[2 * R + r];
 }
 
+// End of an iteration: count it for every column that was active, and stop the columns
+// that converged (rr_new <= rtol^2 yy) or broke down (pAp <= 0 or not finite).
+// cnt[R] is set to 1 on a breakdown.
+__global__ void k_cg_check(double* scal, int R, double rtol2, int* cnt) {
+  const int r = threadIdx.x;
+  if (r >= R || scal[4 * R + r] == 0.0) return;
+  cnt[r] += 1;
+  const double pap = scal[1 * R + r], rrn = scal[2 * R + r];
+  if (!(pap > 0.0) || !isfinite(pap) || !isfinite(rrn)) {
+    scal[4 * R + r] = 0.0;
+    cnt[R] = 1;
+  } else if (rrn <= rtol2 * scal[3 * R + r]) {
+    scal[4 * R + r] = 0.0;
+  }
+}
+
 __global__ void k_axpy_cols(double* __restrict__ y, const double* __restrict__ x, double a, long long total) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
     y[i] += a * x[i];
@@ -123,70 +142,117 @@ void read_scalars(Plan& plan, int R, cudaStream_t st) {
 
 }  // namespace
 
+// iterations per host check (and per captured graph)
+constexpr int kCgBlock = 16;
+
+void cg_iteration(Plan& plan, double* xr, int R, double eta2, double rtol, cudaStream_t st) {
+  const long long n = plan.N;
+  const int nb = red_blocks(n);
+  double* r = plan.cg_r;
+  double* p = plan.cg_p;
+  double* ap = plan.cg_ap;
+  matvec_sorted(plan, p, ap, R, eta2, st);
+  dot(p, ap, n, R, plan.partials, plan.scal, 1, st);
+  k_update_xr<<<dim3(nb, R), kRedThreads, 0, st>>>(xr, r, p, ap, n, plan.scal, R, plan.partials);
+  k_dot_final<<<R, kRedThreads, 0, st>>>(plan.partials, nb, plan.scal, 2, R);
+  k_update_p<<<dim3(nb, R), kRedThreads, 0, st>>>(p, r, n, plan.scal, R);
+  k_roll_scalars<<<1, ((R + 31) / 32) * 32, 0, st>>>(plan.scal, R);
+  k_cg_check<<<1, ((R + 31) / 32) * 32, 0, st>>>(plan.scal, R, rtol * rtol, plan.cg_cnt);
+}
+
+// A graph of kCgBlock iterations for (x, R, eta2, rtol); false when it cannot be made
+// (the caller then launches the iterations directly).
+bool cg_graph(Plan& plan, double* xr, int R, double eta2, double rtol) {
+  CgGraph& g = plan.cg_graph;
+  if (g.exec && g.x == xr && g.R == R && g.eta2 == eta2 && g.rtol == rtol) return true;
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (!plan.cap_stream && cudaStreamCreateWithFlags(&plan.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    plan.cap_stream = nullptr;
+    return false;
+  }
+  if (cudaStreamBeginCapture(plan.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  bool ok = true;
+  try {
+    for (int i = 0; i < kCgBlock; ++i) cg_iteration(plan, xr, R, eta2, rtol, plan.cap_stream);
+  } catch (const Error&) {
+    ok = false;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(plan.cap_stream, &graph);
+  ok = ok && e == cudaSuccess && graph != nullptr;
+  if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    g.exec = nullptr;
+    return false;
+  }
+  g.x = xr;
+  g.R = R;
+  g.eta2 = eta2;
+  g.rtol = rtol;
+  return true;
+}
+
 int cg_solve_sorted(Plan& plan, const double* y_sorted, double* x_sorted, int R, double eta2, double rtol, int maxit,
                     int* iters, double* relres, cudaStream_t st) {
   const long long n = plan.N;
   const size_t bytes = sizeof(double) * n * R;
   double* xr = x_sorted;
-  double* r = plan.cg_r;
-  double* p = plan.cg_p;
-  double* ap = plan.cg_ap;
   GPN_CUDA(cudaMemsetAsync(xr, 0, bytes, st));
-  GPN_CUDA(cudaMemcpyAsync(r, y_sorted, bytes, cudaMemcpyDeviceToDevice, st));
-  GPN_CUDA(cudaMemcpyAsync(p, y_sorted, bytes, cudaMemcpyDeviceToDevice, st));
-  dot(r, r, n, R, plan.partials, plan.scal, 0, st);
+  GPN_CUDA(cudaMemcpyAsync(plan.cg_r, y_sorted, bytes, cudaMemcpyDeviceToDevice, st));
+  GPN_CUDA(cudaMemcpyAsync(plan.cg_p, y_sorted, bytes, cudaMemcpyDeviceToDevice, st));
+  GPN_CUDA(cudaMemsetAsync(plan.cg_cnt, 0, sizeof(int) * (R + 1), st));
+  dot(plan.cg_r, plan.cg_r, n, R, plan.partials, plan.scal, 0, st);
   dot(y_sorted, y_sorted, n, R, plan.partials, plan.scal, 3, st);
   read_scalars(plan, R, st);
   std::vector<double> hs(plan.host_scal, plan.host_scal + 5 * R);
-  std::vector<int> it(R, 0);
-  std::vector<char> active(R, 1);
+  bool any = false;
   for (int c = 0; c < R; ++c) {
-    double yy = hs[3 * R + c];
-    if (yy == 0.0 || std::sqrt(hs[0 * R + c] / yy) <= rtol) active[c] = 0;
-    hs[4 * R + c] = active[c] ? 1.0 : 0.0;
+    const double yy = hs[3 * R + c];
+    const bool active = !(yy == 0.0 || std::sqrt(hs[0 * R + c] / yy) <= rtol);
+    hs[4 * R + c] = active ? 1.0 : 0.0;
+    any = any || active;
   }
   GPN_CUDA(cudaMemcpyAsync(plan.scal + 4 * R, &hs[4 * R], sizeof(double) * R, cudaMemcpyHostToDevice, st));
-  int status = GP_OK;
-  int nb = red_blocks(n);
-  for (int iter = 0; iter < maxit; ++iter) {
-    bool any = false;
-    for (int c = 0; c < R; ++c) any = any || active[c];
-    if (!any) break;
-    matvec_sorted(plan, p, ap, R, eta2, st);
-    dot(p, ap, n, R, plan.partials, plan.scal, 1, st);
-    k_update_xr<<<dim3(nb, R), kRedThreads, 0, st>>>(xr, r, p, ap, n, plan.scal, R, plan.partials);
-    k_dot_final<<<R, kRedThreads, 0, st>>>(plan.partials, nb, plan.scal, 2, R);
-    k_update_p<<<dim3(nb, R), kRedThreads, 0, st>>>(p, r, n, plan.scal, R);
-    k_roll_scalars<<<1, ((R + 31) / 32) * 32, 0, st>>>(plan.scal, R);
-    read_scalars(plan, R, st);
-    for (int c = 0; c < R; ++c) {
-      if (!active[c]) continue;
-      double pap = plan.host_scal[1 * R + c];
-      double rrn = plan.host_scal[2 * R + c];
-      it[c] += 1;
-      if (!(pap > 0.0) || !std::isfinite(pap) || !std::isfinite(rrn)) {
-        status = GP_EBREAKDOWN;
-        active[c] = 0;
-      } else if (std::sqrt(rrn / plan.host_scal[3 * R + c]) <= rtol) {
-        active[c] = 0;
-      }
+  // graphs need no profiling events inside, and the first iterations create any lazy
+  // transform plans outside a capture
+  const bool use_graph = !plan.prof.on;
+  bool captured = false;
+  int done = 0;
+  while (any && done < maxit) {
+    const int k = std::min(kCgBlock, maxit - done);
+    if (use_graph && k == kCgBlock && done > 0 && (captured || cg_graph(plan, xr, R, eta2, rtol))) {
+      captured = true;
+      GPN_CUDA(cudaGraphLaunch(plan.cg_graph.exec, st));
+    } else {
+      for (int i = 0; i < k; ++i) cg_iteration(plan, xr, R, eta2, rtol, st);
     }
-    // deactivate finished columns on the device before the next iteration
-    for (int c = 0; c < R; ++c) hs[4 * R + c] = active[c] ? 1.0 : 0.0;
-    GPN_CUDA(cudaMemcpyAsync(plan.scal + 4 * R, &hs[4 * R], sizeof(double) * R, cudaMemcpyHostToDevice, st));
-    GPN_CUDA(cudaStreamSynchronize(st));
+    done += k;
+    read_scalars(plan, R, st);
+    any = false;
+    for (int c = 0; c < R; ++c) any = any || plan.host_scal[4 * R + c] != 0.0;
   }
+  std::vector<int> cnt(R + 1, 0);
+  GPN_CUDA(cudaMemcpyAsync(cnt.data(), plan.cg_cnt, sizeof(int) * (R + 1), cudaMemcpyDeviceToHost, st));
   read_scalars(plan, R, st);
   bool unconverged = false;
   for (int c = 0; c < R; ++c) {
-    double yy = plan.host_scal[3 * R + c];
-    double rel = yy > 0.0 ? std::sqrt(plan.host_scal[0 * R + c] / yy) : 0.0;
-    if (iters) iters[c] = it[c];
+    const double yy = plan.host_scal[3 * R + c];
+    const double rel = yy > 0.0 ? std::sqrt(plan.host_scal[0 * R + c] / yy) : 0.0;
+    if (iters) iters[c] = cnt[c];
     if (relres) relres[c] = rel;
-    if (active[c]) unconverged = true;
+    if (plan.host_scal[4 * R + c] != 0.0) unconverged = true;
   }
-  if (status == GP_OK && unconverged) status = GP_ENOTCONV;
-  return status;
+  if (cnt[R]) return GP_EBREAKDOWN;
+  return unconverged ? GP_ENOTCONV : GP_OK;
 }
 
 int cg_refined_sorted(Plan& lo, Plan& hi, const double* y_hi_sorted, double* x_hi_sorted, int R, double eta2,

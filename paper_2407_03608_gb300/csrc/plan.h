@@ -54,6 +54,14 @@ struct PhaseProfile {
   void destroy();
 };
 
+// A CUDA graph of a block of CG iterations, valid for one (x, R, eta2, rtol).
+struct CgGraph {
+  cudaGraphExec_t exec = nullptr;
+  double* x = nullptr;
+  int R = 0;
+  double eta2 = 0.0, rtol = 0.0;
+};
+
 struct Plan {
   int device = 0;
   PhaseProfile prof;
@@ -91,6 +99,9 @@ struct Plan {
   double* cg_ap = nullptr;
   double* cg_y = nullptr;
   double* scal = nullptr;               // device scalars (see cg.cu)
+  int* cg_cnt = nullptr;                // CG iterations per column, then a breakdown flag
+  CgGraph cg_graph;                     // captured block of CG iterations
+  cudaStream_t cap_stream = nullptr;    // stream the graph is captured on
   double* partials = nullptr;           // reduction partials
   double* host_scal = nullptr;          // pinned mirror
   double* stage_in = nullptr;           // staging for host-pointer calls, N * max_rhs
