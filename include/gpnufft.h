@@ -176,6 +176,20 @@ int gp_cg_solve_refined(gp_plan_t plan_lo, gp_plan_t plan_hi, const double* y, d
 int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, long long Nq, const double* field_aq,
                       const double* field_bq, double* mu, void* cuda_stream);
 
+/* Posterior variance of the latent function at the training points: the diagonal of
+ * Eq. (postcov) with K~, which equals eta2 - eta2^2 [(K~ + eta2 I)^{-1}]_ii.  The
+ * diagonal of the inverse is estimated from R probe vectors z_r (entries +-1 give the
+ * Hutchinson-type estimator; the estimator is an extension, the paper has none):
+ *   d_i = (sum_r z_ri x_ri) / (sum_r z_ri^2),  x_r = (K~ + eta2 I)^{-1} z_r by CG
+ * (gp_cg_solve's iteration, max_rhs probes per batch).
+ *   probes : N x R column-major float64, original point order (host or device).
+ *   eta2 > 0; rtol, maxit as gp_cg_solve.
+ *   var : N float64.   iters_out : R ints (host, may be NULL).
+ * Errors: GP_EINVAL, GP_ENOTCONV (some probe stopped at maxit; var is still written),
+ * GP_EBREAKDOWN, GP_ECUDA, GP_ECUFFT. */
+int gp_posterior_variance(gp_plan_t plan, const double* probes, int R, double eta2, double rtol, int maxit,
+                          double* var, int* iters_out, void* cuda_stream);
+
 /* Largest query batch of gp_posterior_mean_noalloc (sizes its static scratch). */
 #define GP_NOALLOC_MAX_QUERIES 32768
 

@@ -18,9 +18,10 @@ import numpy as np
 from . import abi
 from .abi import (GP_FP32, GP_FP64, GP_MATERN, GP_PARAMS_PAPER, GP_PARAMS_SCALES, GP_SE, GPError,  # noqa: F401
                   gp_cg_solve, gp_cg_solve_refined, gp_destroy, gp_matvec, gp_plan, gp_profile_enable, gp_profile_read,
-                  gp_plan_info_get, gp_posterior_mean, gp_version)
+                  gp_plan_info_get, gp_posterior_mean, gp_posterior_variance, gp_version)
 
 __all__ = ["Plan", "GPError", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined", "gp_posterior_mean",
+           "gp_posterior_variance",
            "gp_profile_enable", "gp_profile_read",
            "gp_plan_info_get", "gp_destroy", "gp_version", "GP_FP32", "GP_FP64", "GP_MATERN", "GP_SE",
            "GP_PARAMS_SCALES", "GP_PARAMS_PAPER"]
@@ -138,6 +139,14 @@ class Plan:
         mu = _like(alpha, (xq.shape[0],))
         gp_posterior_mean(self._h, alpha, xq, field_aq, field_bq, mu, stream)
         return mu
+
+    def posterior_variance(self, probes, eta2: float, rtol: float = 1e-8, maxit: int = 10000, stream=None):
+        """Posterior variance at the training points from (N, R) probe vectors (entries +-1):
+        eta2 - eta2^2 diag((K~ + eta2 I)^{-1}), the diagonal estimated from the probes."""
+        buf, R, one = _as_cols(probes)
+        var = _like(buf, (int(self.info["N"]),))
+        st, iters = gp_posterior_variance(self._h, buf, R, eta2, rtol, maxit, var, stream)
+        return var, {"status": st, "iters": iters}
 
     def matched_opts(self):
         """Overrides that rebuild exactly this plan's K~ (for a second precision)."""

@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "GP_OK", -1: "GP_EINVAL", -2: "GP_ENOMEM", -3: "GP_ECUDA", -4
 
 #: every symbol include/gpnufft.h declares
 EXPORTED = ["gp_plan_opts_default", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined",
-            "gp_posterior_mean", "gp_posterior_mean_noalloc", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
+            "gp_posterior_mean", "gp_posterior_mean_noalloc", "gp_posterior_variance", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
             "gp_version"]
 
 
@@ -91,6 +91,9 @@ def _load():
     lib.gp_cg_solve_refined.restype = ctypes.c_int
     lib.gp_posterior_mean.argtypes = [vp, dp, dp, ctypes.c_longlong, dp, dp, dp, vp]
     lib.gp_posterior_mean.restype = ctypes.c_int
+    lib.gp_posterior_variance.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp,
+                                          ip, vp]
+    lib.gp_posterior_variance.restype = ctypes.c_int
     lib.gp_posterior_mean_noalloc.argtypes = [vp, dp, dp, ctypes.c_longlong, dp, dp, dp, vp]
     lib.gp_posterior_mean_noalloc.restype = ctypes.c_int
     lib.gp_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -219,6 +222,16 @@ def gp_posterior_mean(plan, alpha, xq, field_aq, field_bq, mu, stream=None):
     mp, mk = ptr_of(mu)
     return check(LIB.gp_posterior_mean(plan, ap, qp, int(xq.shape[0]), fa, fb, mp,
                                        stream if stream is not None else current_stream()))
+
+
+def gp_posterior_variance(plan, probes, R: int, eta2: float, rtol: float, maxit: int, var, stream=None):
+    pp, pk = ptr_of(probes)
+    vp_, vk = ptr_of(var)
+    iters = (ctypes.c_int * R)()
+    st = check(LIB.gp_posterior_variance(plan, pp, int(R), float(eta2), float(rtol), int(maxit), vp_, iters,
+                                         stream if stream is not None else current_stream()),
+               allow=(GP_ENOTCONV,))
+    return st, list(iters)
 
 
 def gp_posterior_mean_noalloc(plan, alpha, xq, field_aq, field_bq, mu, stream=None):

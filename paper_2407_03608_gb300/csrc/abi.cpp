@@ -615,6 +615,49 @@ int gp_posterior_mean(gp_plan_t plan, const double* alpha, const double* xq, lon
   });
 }
 
+int gp_posterior_variance(gp_plan_t plan, const double* probes, int R, double eta2, double rtol, int maxit,
+                          double* var, int* iters_out, void* cuda_stream) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    GPN_CHECK(probes && var, GP_EINVAL, "null probes or var");
+    GPN_CHECK(R >= 1, GP_EINVAL, "R must be >= 1");
+    GPN_CHECK(eta2 > 0.0 && std::isfinite(eta2), GP_EINVAL, "eta2 must be > 0");
+    GPN_CHECK(rtol > 0.0 && maxit >= 1, GP_EINVAL, "rtol > 0 and maxit >= 1 required");
+    const long long n = p->N;
+    const bool dev_probes = is_device_ptr(probes);
+    double* num = p->vec_a;
+    double* den = p->vec_b;
+    GPN_CUDA(cudaMemsetAsync(num, 0, sizeof(double) * n, st));
+    GPN_CUDA(cudaMemsetAsync(den, 0, sizeof(double) * n, st));
+    int status = GP_OK;
+    std::vector<int> it(p->max_rhs);
+    for (int r0 = 0; r0 < R; r0 += p->max_rhs) {
+      const int rc = std::min(p->max_rhs, R - r0);
+      const double* z = probes + (size_t)r0 * n;
+      if (!dev_probes) {
+        GPN_CUDA(cudaMemcpyAsync(p->stage_in, z, sizeof(double) * n * rc, cudaMemcpyHostToDevice, st));
+        z = p->stage_in;
+      }
+      gather_sorted(p->pts, z, p->cg_y, rc, st);
+      const int s = cg_solve_sorted(*p, p->cg_y, p->cg_x, rc, eta2, rtol, maxit, it.data(), nullptr, st);
+      if (s == GP_EBREAKDOWN) fail(GP_EBREAKDOWN, "CG breakdown on a probe");
+      if (s == GP_ENOTCONV) status = GP_ENOTCONV;
+      if (iters_out)
+        for (int c = 0; c < rc; ++c) iters_out[r0 + c] = it[c];
+      probe_accumulate(p->cg_y, p->cg_x, n, rc, num, den, st);
+    }
+    DevOut o(var, p->stage_out, (size_t)n);
+    variance_finish(num, den, n, eta2, p->cg_r, st);
+    scatter_sorted(p->pts, p->cg_r, o.dev, 1, st);
+    GPN_CUDA(cudaGetLastError());
+    o.finish(*p, st);
+    if (status == GP_ENOTCONV) g_last_error = "CG reached maxit before rtol on some probe";
+    return status;
+  });
+}
+
 int gp_posterior_mean_noalloc(gp_plan_t plan, const double* alpha, const double* xq, long long Nq,
                               const double* field_aq, const double* field_bq, double* mu, void* cuda_stream) {
   return guarded([&]() {

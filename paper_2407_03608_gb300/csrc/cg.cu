@@ -125,6 +125,28 @@ __global__ void k_axpy_cols(double* __restrict__ y, const double* __restrict__ x
     y[i] += a * x[i];
 }
 
+// num_i += sum_r z_ri x_ri, den_i += sum_r z_ri^2 (probe estimate of a diagonal)
+__global__ void k_probe_accum(const double* __restrict__ z, const double* __restrict__ x, long long n, int R,
+                              double* __restrict__ num, double* __restrict__ den) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int r = 0; r < R; ++r) {
+      const double zi = z[(size_t)r * n + i];
+      a += zi * x[(size_t)r * n + i];
+      b += zi * zi;
+    }
+    num[i] += a;
+    den[i] += b;
+  }
+}
+
+// var_i = eta2 - eta2^2 num_i / den_i
+__global__ void k_variance_finish(const double* __restrict__ num, const double* __restrict__ den, long long n,
+                                  double eta2, double* __restrict__ var) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    var[i] = den[i] > 0.0 ? eta2 - eta2 * eta2 * (num[i] / den[i]) : eta2;
+}
+
 int red_blocks(long long n) { return (int)std::max<long long>(1, std::min<long long>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads)); }
 
 void dot(const double* u, const double* v, long long n, int R, double* partial, double* scal, int slot,
@@ -253,6 +275,17 @@ int cg_solve_sorted(Plan& plan, const double* y_sorted, double* x_sorted, int R,
   }
   if (cnt[R]) return GP_EBREAKDOWN;
   return unconverged ? GP_ENOTCONV : GP_OK;
+}
+
+void probe_accumulate(const double* z_sorted, const double* x_sorted, long long n, int R, double* num, double* den,
+                      cudaStream_t st) {
+  k_probe_accum<<<(int)std::min<long long>(4096, (n + 255) / 256), 256, 0, st>>>(z_sorted, x_sorted, n, R, num, den);
+  GPN_CUDA(cudaGetLastError());
+}
+
+void variance_finish(const double* num, const double* den, long long n, double eta2, double* var, cudaStream_t st) {
+  k_variance_finish<<<(int)std::min<long long>(4096, (n + 255) / 256), 256, 0, st>>>(num, den, n, eta2, var);
+  GPN_CUDA(cudaGetLastError());
 }
 
 int cg_refined_sorted(Plan& lo, Plan& hi, const double* y_hi_sorted, double* x_hi_sorted, int R, double eta2,

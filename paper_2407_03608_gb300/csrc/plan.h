@@ -225,6 +225,11 @@ void gather_sorted(const PointSet& ps, const double* src, double* dst, int R, cu
 void scatter_sorted(const PointSet& ps, const double* src, double* dst, int R, cudaStream_t st);
 
 // CG in sorted order (cg.cu).
+// Probe estimate of a diagonal: num += sum_r z_r * x_r, den += sum_r z_r^2 (sorted
+// order, n entries); then var = eta2 - eta2^2 num / den.
+void probe_accumulate(const double* z_sorted, const double* x_sorted, long long n, int R, double* num, double* den,
+                      cudaStream_t st);
+void variance_finish(const double* num, const double* den, long long n, double eta2, double* var, cudaStream_t st);
 int cg_solve_sorted(Plan& plan, const double* y_sorted, double* x_sorted, int R, double eta2, double rtol,
                     int maxit, int* iters, double* relres, cudaStream_t st);
 int cg_refined_sorted(Plan& lo, Plan& hi, const double* y_sorted, double* x_sorted, int R, double eta2,
