@@ -208,3 +208,11 @@ def serving_stream(n_requests: int = 2000, rate_hz: float = 50.0, n_min: int = 1
         y = g.random((n, r)) if r > 1 else g.random(n)
         out.append(Request(rid, t, x, s, l, nu, 0.1, y))
     return out
+
+
+def paper_setup(n: int, d: int, seed: int = 0):
+    """The setup of the paper's experiments (Sec. 6): x ~ U[-1, 1]^d, w(x) = 1 and
+    sigma(x) = (prod_i cos(pi x_i) + 2) / 6, in the paper's own (w, sigma) fields."""
+    x = _rng(seed).uniform(-1.0, 1.0, (n, d))
+    sigma = (np.prod(np.cos(np.pi * x), axis=1) + 2.0) / 6.0
+    return x, np.ones(n), sigma
