@@ -120,11 +120,47 @@ struct RowsArgs {
   int col_lo, col_hi;
 };
 
-// In-place complex FFT of length 2^L on the row buffer b, NT = 2^L / 16 threads per
-// row (t = 0..NT-1), every thread of the block taking part in the barriers.  tw2: the
-// two-level twiddle of the length-2^L FFT; ptab: the staged pass tables (FP32).
+// In-place complex FFT of length N = 2^L on the row buffer b by Stockham passes (one of
+// radix 2^(L mod 4) when L is not a multiple of 4, then radix 16), NT = N / 16 threads per
+// row (t = 0..NT-1), every thread of the block taking part in the barriers.  The first
+// pass takes its inputs from x[u] = element t + u N/16 (the values the thread loaded
+// from global memory), which skips a shared-memory round trip.  tw2: the two-level
+// twiddle; ptab: the staged pass tables (FP32 forward).
 template <bool INV, int L, typename T>
-__device__ __forceinline__ void fft_block(cpx<T>* b, const fft::Twiddle2<T>& tw2, const cpx<T>* ptab, int t) {
+__device__ __forceinline__ void fft_block_from_regs(cpx<T>* b, const cpx<T> (&x)[16], const fft::Twiddle2<T>& tw2,
+                                                    const cpx<T>* ptab, int t) {
+  constexpr int N = 1 << L, NT = N / 16;
+  constexpr int R0 = (L % 4 == 0) ? 16 : (1 << (L % 4));
+  {
+    fft::Pass<R0, 16 / R0, T> p;
+    fft::first_pass_inputs(p, x);
+    p.template compute<INV>(tw2, N, 1, t, NT);  // span 1: no twiddles
+    p.write(b, 1, t, NT);
+  }
+  __syncthreads();
+  int Ns = R0;
+#pragma unroll
+  for (int s = (L % 4 == 0) ? 1 : 0; s < L / 4; ++s) {
+    fft::Pass<16, 1, T> p;
+    p.load(b, N, t, NT);
+    __syncthreads();
+    if constexpr (pass_tables_in_smem<T, INV>()) {
+      const fft::PassTwiddle<T> tw{ptab + fft::pass_table_offset(L, Ns), Ns};
+      p.template store<INV>(b, tw, N, Ns, t, NT);
+    } else {
+      p.template store<INV>(b, tw2, N, Ns, t, NT);
+    }
+    __syncthreads();
+    Ns *= 16;
+  }
+}
+
+// The same transform from the buffer, except that the last pass (radix 16 at span N/16)
+// hands its outputs to out(r, v) instead of the buffer: output r of thread t is element
+// t + r N/16 of the transform.  No barrier follows.
+template <bool INV, int L, typename T, typename Out>
+__device__ __forceinline__ void fft_block_to(cpx<T>* b, const fft::Twiddle2<T>& tw2, const cpx<T>* ptab, int t,
+                                             Out out) {
   constexpr int N = 1 << L, NT = N / 16;
   int Ns = 1;
   if constexpr (L % 4 != 0) {
@@ -143,11 +179,17 @@ __device__ __forceinline__ void fft_block(cpx<T>* b, const fft::Twiddle2<T>& tw2
     __syncthreads();
     if constexpr (pass_tables_in_smem<T, INV>()) {
       const fft::PassTwiddle<T> tw{ptab + fft::pass_table_offset(L, Ns), Ns};
-      p.template store<INV>(b, tw, N, Ns, t, NT);
+      p.template compute<INV>(tw, N, Ns, t, NT);
     } else {
-      p.template store<INV>(b, tw2, N, Ns, t, NT);
+      p.template compute<INV>(tw2, N, Ns, t, NT);
     }
-    __syncthreads();
+    if (s + 1 < L / 4) {
+      p.write(b, Ns, t, NT);
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) out(r, p.v[0][r]);
+    }
     Ns *= 16;
   }
 }
@@ -210,15 +252,13 @@ __global__ void __launch_bounds__(RB*(1 << L) / 16, (rows_min_blocks<T, L, RB>()
           v[u] = {w.x, w.y};
         }
       }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) b[fft::pad(t + u * NT)] = v[u];  // z[i] = x[2i] + i x[2i+1]
+      if (first) {
+        cp_async_wait_all();
+        first = false;
+      }
+      __syncthreads();  // twiddles staged; the previous item's buffers are free
+      fft_block_from_regs<false, L>(b, v, tw, ptab, t);  // z[i] = x[2i] + i x[2i+1]
     }
-    if (first) {
-      cp_async_wait_all();
-      first = false;
-    }
-    __syncthreads();
-    fft_block<false, L>(b, tw, ptab, t);
     // real split of the RB rows at m = 0..M; the RB values of one m are adjacent in X
     cpx<T>* dst = a.X + (size_t)cr * (a.M + 1) * a.nf + y0;
     for (int m = threadIdx.x; m <= a.M; m += blockDim.x) {
@@ -297,17 +337,16 @@ __global__ void __launch_bounds__(RB*(1 << L) / 16, (rows_min_blocks<T, L, RB>()
       br[fft::pad(k)] = zk;
     }
     __syncthreads();
-    fft_block<true, L>(b, tw, ptab, t);
-    if (y < a.row_hi) {
+    {
+      // the last pass writes x[2i], x[2i+1] (i = t + r NT) straight to the grid row
       T* dst = a.gout + (size_t)cr * a.G + y * a.nf;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int i = t + u * NT;
-        if (2 * i + 1 >= a.col_lo && 2 * i < a.col_hi) {
-          const cpx<T> v = b[fft::pad(i)];
+      const bool rin = y < a.row_hi;
+      const int clo = a.col_lo, chi = a.col_hi;
+      fft_block_to<true, L>(b, tw, ptab, t, [&](int r, const cpx<T>& v) {
+        const int i = t + r * NT;
+        if (rin && 2 * i + 1 >= clo && 2 * i < chi)
           *reinterpret_cast<typename Vec2<T>::type*>(dst + 2 * i) = {v.x, v.y};
-        }
-      }
+      });
     }
     __syncthreads();  // the buffers are refilled by the next item
   }

@@ -165,8 +165,9 @@ struct Pass {
     }
   }
 
+  // twiddles and the DFT-R of every butterfly, in registers
   template <bool INV, typename TW>
-  GPN_HD void store(cpx<T>* buf, const TW& tw, int N, int Ns, int t, int nthreads) {
+  GPN_HD void compute(const TW& tw, int N, int Ns, int t, int nthreads) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = t + b * nthreads;
@@ -181,12 +182,38 @@ struct Pass {
         }
       }
       dft<INV, R>(v[b]);
+    }
+  }
+
+  // the outputs to their Stockham positions
+  GPN_HD void write(cpx<T>* buf, int Ns, int t, int nthreads) const {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = t + b * nthreads;
+      const int k = j & (Ns - 1);
       const int base = (j - k) * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) buf[pad(base + r * Ns)] = v[b][r];
     }
   }
+
+  template <bool INV, typename TW>
+  GPN_HD void store(cpx<T>* buf, const TW& tw, int N, int Ns, int t, int nthreads) {
+    compute<INV>(tw, N, Ns, t, nthreads);
+    write(buf, Ns, t, nthreads);
+  }
 };
+
+// Register view of the first pass: with nthreads = N / 16, the elements
+// t + u * nthreads (u = 0..15) that a thread holds are exactly the inputs of its
+// butterflies in the first pass (radix R at span 1): butterfly b, input r is u = b + r 16/R.
+template <int R, int NB, typename T>
+GPN_HD void first_pass_inputs(Pass<R, NB, T>& p, const cpx<T> (&x)[16]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int r = 0; r < R; ++r) p.v[b][r] = x[b + r * (16 / R)];
+}
 
 // W_N^i from two short tables, W_N^i = W_N^{64 (i / 64)} W_N^{i mod 64}: hi[q] = W_N^{64 q}
 // (q < N / 64, at least one entry), lo[j] = W_N^j (j < 64).  One complex product per

@@ -42,6 +42,43 @@ void pass16(std::vector<C>& buf, const std::vector<C>& tab, int L, int Ns) {
   for (int t = 0; t < nt; ++t) st[t].template store<INV>(buf.data(), tw, N, Ns, t, nt);
 }
 
+// the first pass from each thread's registers x[u] = element t + u N/16 (as the device
+// row kernels do), then the remaining passes as usual
+template <int R, int NB, bool INV>
+void first_from_regs(std::vector<C>& buf, int N) {
+  const int nt = N / 16;
+  std::vector<Pass<R, NB, double>> st(nt);
+  for (int t = 0; t < nt; ++t) {
+    C x[16];
+    for (int u = 0; u < 16; ++u) x[u] = buf[gpn::fft::pad(t + u * nt)];
+    gpn::fft::first_pass_inputs(st[t], x);
+  }
+  const gpn::fft::Twiddle2<double> none{nullptr, nullptr};  // span 1: no twiddles are read
+  for (int t = 0; t < nt; ++t) {
+    st[t].template compute<INV>(none, N, 1, t, nt);
+    st[t].write(buf.data(), 1, t, nt);
+  }
+}
+
+template <bool INV>
+void fft_regs(std::vector<C>& buf, int L) {
+  const int N = 1 << L;
+  const std::vector<double> raw = gpn::fft::pass_tables(L);
+  std::vector<C> tab(raw.size() / 2 + 1);
+  for (size_t i = 0; i < raw.size() / 2; ++i) tab[i] = {raw[2 * i], raw[2 * i + 1]};
+  int Ns = 1;
+  switch (L % 4) {
+    case 1: first_from_regs<2, 8, INV>(buf, N); Ns = 2; break;
+    case 2: first_from_regs<4, 4, INV>(buf, N); Ns = 4; break;
+    case 3: first_from_regs<8, 2, INV>(buf, N); Ns = 8; break;
+    default: first_from_regs<16, 1, INV>(buf, N); Ns = 16; break;
+  }
+  for (int q = (L % 4 == 0) ? 1 : 0; q < L / 4; ++q) {
+    pass16<INV>(buf, tab, L, Ns);
+    Ns *= 16;
+  }
+}
+
 template <bool INV>
 void fft(std::vector<C>& buf, int L) {
   const int N = 1 << L;
@@ -70,7 +107,15 @@ int main() {
   auto at = [&](int i) -> C& { return buf[gpn::fft::pad(i)]; };
   std::vector<C> wnf(N + 1);
   for (int k = 0; k <= N; ++k) wnf[k] = {std::cos(M_PI * k / N), -std::sin(M_PI * k / N)};  // W_{2N}^k
-  if (!std::strcmp(mode, "c2c") || !std::strcmp(mode, "ic2c")) {
+  if (!std::strcmp(mode, "c2cr")) {
+    for (int i = 0; i < N; ++i) {
+      double re, im;
+      if (std::scanf("%lf %lf", &re, &im) != 2) return 1;
+      at(i) = {re, im};
+    }
+    fft_regs<false>(buf, L);
+    for (int i = 0; i < N; ++i) std::printf("%.17g\n%.17g\n", at(i).x, at(i).y);
+  } else if (!std::strcmp(mode, "c2c") || !std::strcmp(mode, "ic2c")) {
     for (int i = 0; i < N; ++i) {
       double re, im;
       if (std::scanf("%lf %lf", &re, &im) != 2) return 1;
