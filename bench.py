@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -127,23 +128,46 @@ def workload(args):
 
 
 def algorithmic_bytes(info, N, R, rs):
-    """Algorithmic HBM bytes per launch of each matvec phase (reads + writes once)."""
-    d, nf, M = info["d"], info["nf"], info["M"]
+    """Algorithmic HBM bytes per launch of each matvec phase (reads + writes once).
+
+    ext = the grid rows/columns that hold data (the point box on the fine grid plus one
+    kernel width); cplx = 2 rs.  Transform 3 (d = 2): the row stages read/write ext^2
+    real values and (M+1) ext modes per channel, the column transforms (M+1) nf complex
+    each way, step 3 the mode box (M+1)(2M+1) plus A' on the quadrant (M+1)^2."""
+    d, nf, M, W = info["d"], info["nf"], info["M"], info["kernel_width"]
     C = info["n_sigma"] + 1
-    G = nf ** d
-    S = nf ** (d - 1) * (nf // 2 + 1)
-    nfreq = (2 * M + 1) ** (d - 1) * (M + 1)
     L = max(info["box_hi"][a] - info["box_lo"][a] for a in range(d))
-    P = 1.0 / info["dw"]
-    occ = min(1.0, (L / P + (info["kernel_width"] + info["tile"]) / nf)) ** d
+    ext = min(nf, int(math.ceil(nf * info["dw"] * L)) + W)
+    G, Gocc = nf ** d, ext ** d
+    cp = 2 * rs
     pts = N * (d * (4 + rs) + C * rs + 4)          # l0, xi, w_k, bin pointers
-    return {
-        "spread": C * R * G * rs + pts + N * R * 8,
-        "fft_fwd": C * R * (G * rs + S * 2 * rs),
-        "diag": C * R * nfreq * 2 * rs + (C * (C + 1) // 2) * nfreq * rs + C * R * S * 2 * rs,
-        "fft_inv": C * R * (S * 2 * rs + G * rs),
-        "interp": C * R * G * occ * rs + pts + 2 * N * R * 8,
-    }
+    pairs = C * (C + 1) // 2
+    out = {"spread": C * R * Gocc * rs + pts + N * R * 8, "interp": C * R * Gocc * rs + pts + 2 * N * R * 8}
+    if info["transform"] == 3:
+        rows = C * R * (Gocc * rs + (M + 1) * ext * cp)
+        cols = 2 * C * R * (M + 1) * nf * cp
+        box = C * R * (M + 1) * (2 * M + 1) * cp
+        out.update(fft_fwd=rows + cols, fft_inv=rows + cols, diag=2 * box + pairs * (M + 1) ** 2 * rs)
+    else:
+        S = nf ** (d - 1) * (nf // 2 + 1)
+        nfreq = (2 * M + 1) ** (d - 1) * (M + 1)
+        out.update(fft_fwd=C * R * (G * rs + S * cp), fft_inv=C * R * (S * cp + G * rs),
+                   diag=C * R * nfreq * cp + pairs * nfreq * rs + C * R * S * cp)
+    return out
+
+
+# DRAM bytes per launch from one ncu capture of the current kernels on the 2-D clustered
+# workload (N = 1e6, eps = 1e-6, FP32, transform 3): profiles/matvec_kernels_d2_N1e6_clustered.md.
+# Reported as `traffic` only for that workload; to be re-taken whenever these kernels change.
+MEASURED_TRAFFIC = {
+    ("d2_N1000000_clustered_matern32", "f32", 1e-06): {
+        "spread": 0.061e9 + 1.078e9,
+        "fft_fwd": (1.174e9 + 1.109e9) + (1.663e9 + 1.607e9),
+        "diag": 2.586e9 + 1.111e9,
+        "fft_inv": (1.663e9 + 1.607e9) + (1.158e9 + 1.108e9),
+        "interp": 1.196e9 + 0.008e9,
+    },
+}
 
 
 PHASES = ["spread", "fft_fwd", "diag", "fft_inv", "interp"]
@@ -258,10 +282,14 @@ def run_ours(args, ws, rank, local):
     dom_ours = max(ours, key=lambda q: phase_ms[q])
     peak, peak_src = measured_peaks()
 
+    traffic = MEASURED_TRAFFIC.get((w.name, "f32" if prec == gpn.GP_FP32 else "f64", w.eps), {})
+
     def roof(q):
         ach = ab[PHASES[q]] / (phase_ms[q] * 1e-3) / 1e9
+        tr = traffic.get(PHASES[q])
         return {"kernel": PHASES[q], "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "peak_source": peak_src, "traffic": None,
+                "frac": round(ach / peak, 4), "peak_source": peak_src,
+                "traffic": int(tr) if tr is not None and args.n == 1_000_000 else None,
                 "algorithmic_bytes": int(ab[PHASES[q]]), "ms_per_launch": round(phase_ms[q], 4)}
 
     result = {
