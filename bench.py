@@ -156,9 +156,10 @@ def algorithmic_bytes(info, N, R, rs):
     return out
 
 
-# DRAM bytes per launch from one ncu capture of the current kernels on the 2-D clustered
-# workload (N = 1e6, eps = 1e-6, FP32, transform 3): profiles/matvec_kernels_d2_N1e6_clustered.md.
-# Reported as `traffic` only for that workload; to be re-taken whenever these kernels change.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu capture of
+# the current kernels on the 2-D clustered workload (N = 1e6, eps = 1e-6, FP32, transform 3):
+# rows + column transform for the FFT phases.  Reported as `traffic` only for that workload,
+# and to be re-taken whenever these kernels change.
 MEASURED_TRAFFIC = {
     ("d2_N1000000_clustered_matern32", "f32", 1e-06): {
         "spread": 0.061e9 + 1.078e9,
