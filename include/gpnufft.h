@@ -100,6 +100,18 @@ typedef struct gp_plan_opts {
                                contiguous column, step 3 on the mode box only    */
   int max_rhs;            /* largest R the plan will be called with (default 1)         */
   long long max_bytes;    /* refuse plans whose resident device bytes exceed this (0 = no limit) */
+  int step3;              /* step (3) of Sec. 4.2:
+                             0 auto: 1 unless the tensor alone would break max_bytes or
+                               the free device memory, then 2;
+                             1 the stored tensor A[n] of Remark rem:step3 (deconvolutions
+                               folded in; C(C+1)/2 reals per frequency of the half box);
+                             2 memory-lean: a_k = sum_j v~_j G^_kj sum_l G^_lj b_l formed
+                               per frequency from the separable per-dimension factors of
+                               G^ (C (N_t+1) (M+1) reals in total), the sequential
+                               processing over j and k the paper gives as the
+                               alternative to storing A; about 4.5 C (N_t+1)
+                               multiply-adds per frequency.  Not with transform 2
+                               (GP_EUNSUPPORTED).                                        */
 } gp_plan_opts;
 
 typedef struct gp_plan_info {
@@ -116,6 +128,7 @@ typedef struct gp_plan_info {
   double est_err_t, est_err_sigma, est_err_trunc, est_err_alias; /* stage estimates, relative entrywise */
   long long bytes_resident;                /* device bytes the plan holds                 */
   int max_rhs;
+  int step3;                               /* step-3 form in use: 1 tensor, 2 memory-lean */
 } gp_plan_info;
 
 /* Fill opts with the defaults (all zero except max_rhs = 1). */

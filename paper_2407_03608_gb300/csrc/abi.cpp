@@ -365,16 +365,6 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->grid_elems = G;
   plan->spec_elems = S;
   plan->n_freq = nfreq;
-  long long est = (long long)(C * (long long)max_rhs * (2 * G * rs + S * 2 * rs)) * 2  // grids + transforms
-                  + (long long)(C * (C + 1) / 2) * nfreq * (long long)rs + N * (long long)(d * (4 + rs) + 4 + C * rs) +
-                  (long long)N * max_rhs * 8 * 9;
-  GPN_CHECK(o.max_bytes <= 0 || est <= o.max_bytes, GP_ENOMEM,
-            "plan needs about " + std::to_string(est) + " device bytes, above max_bytes");
-
-  std::vector<int> bstart;
-  build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
-  build_active_tiles(*plan, bstart);
-  if (spread2d_supported(*plan)) build_spread2d_tiles(*plan, bstart);
   GPN_CHECK(o.transform >= 0 && o.transform <= 3, GP_EINVAL, "transform must be 0, 1, 2 or 3");
   const bool row_ok = rowfft_supported(d, h.nf, rs);
   const bool t3_ok = tr3_supported(d, h.nf, rs);
@@ -388,8 +378,49 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
     nfreq = (h.M + 1) * (h.M + 1);
     plan->n_freq = nfreq;
   }
-  plan->a_tensor = plan->alloc((size_t)(C * (C + 1) / 2) * nfreq * rs);
-  build_a_tensor(*plan, st);
+  const long long a_bytes = (long long)(C * (C + 1) / 2) * nfreq * (long long)rs;
+  const long long lean_bytes =
+      (long long)plan->tb.vt.size() * (h.M + 1) * lean_channel_pitch(C, rs) * (long long)rs;
+  // the large allocations: spreading and interpolation grids, spectra or the pruned
+  // transforms' column buffers, per-point data and the nine work vectors
+  const long long CR = (long long)C * max_rhs;
+  const long long spectra = (plan->tr3 || plan->rowfft)
+                                ? 3 * (d == 2 ? h.nf : 1) * CR * (h.M + 1) * 2 * (long long)rs
+                                : CR * S * 2 * (long long)rs;
+  const long long est_rest = 2 * CR * G * (long long)rs + spectra + N * (long long)(d * (4 + rs) + 8 + C * rs) +
+                             (long long)N * max_rhs * 8 * 9;
+  // step 3: the stored tensor A' (1) or the memory-lean form from per-dimension
+  // factors (2); auto takes the tensor unless it alone breaks max_bytes or the free
+  // device memory
+  GPN_CHECK(o.step3 >= 0 && o.step3 <= 2, GP_EINVAL, "step3 must be 0, 1 or 2");
+  GPN_CHECK(o.step3 != 2 || !plan->rowfft, GP_EUNSUPPORTED,
+            "the memory-lean step 3 runs with transform 1 or 3, not the pruned row transforms");
+  if (o.step3 == 2) {
+    plan->lean = true;
+  } else if (o.step3 == 0 && !plan->rowfft) {
+    size_t free_b = 0, total_b = 0;
+    GPN_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const long long with_a = est_rest + a_bytes, with_f = est_rest + lean_bytes;
+    const bool over_budget = o.max_bytes > 0 && with_a > o.max_bytes && with_f <= o.max_bytes;
+    const bool over_free = with_a > (long long)free_b && with_f <= (long long)free_b;
+    plan->lean = over_budget || over_free;
+  }
+  const long long est = est_rest + (plan->lean ? lean_bytes : a_bytes);
+  GPN_CHECK(o.max_bytes <= 0 || est <= o.max_bytes, GP_ENOMEM,
+            "plan needs about " + std::to_string(est) + " device bytes, above max_bytes");
+
+  std::vector<int> bstart;
+  build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
+  build_active_tiles(*plan, bstart);
+  if (spread2d_supported(*plan)) build_spread2d_tiles(*plan, bstart);
+  if (plan->lean) {
+    build_lean_tables(*plan);
+    GPN_CHECK(lean_smem_bytes(*plan) <= (size_t(200) << 10), GP_EUNSUPPORTED,
+              "memory-lean step 3: the per-block factor table does not fit in shared memory");
+  } else {
+    plan->a_tensor = plan->alloc((size_t)a_bytes);
+    build_a_tensor(*plan, st);
+  }
   plan->grid = plan->alloc((size_t)C * max_rhs * G * rs);
   GPN_CUDA(cudaMemsetAsync(plan->grid, 0, (size_t)C * max_rhs * G * rs, st));
   plan->grid_out = plan->alloc((size_t)C * max_rhs * G * rs);
@@ -765,6 +796,7 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->est_err_alias = h.est_alias;
     info->bytes_resident = p->bytes;
     info->max_rhs = p->max_rhs;
+    info->step3 = p->lean ? 2 : 1;
     return GP_OK;
   });
 }

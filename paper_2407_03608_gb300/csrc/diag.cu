@@ -134,6 +134,7 @@ void diag_impl(Plan& plan, int R, cudaStream_t st) {
 }  // namespace
 
 void launch_diag(Plan& plan, int R, cudaStream_t st) {
+  if (plan.lean) return launch_step3_lean(plan, R, st);
   if (plan.tr3) return tr3_diag(plan, R, st);
   if (plan.rowfft) return rowfft_diag(plan, R, st);
   if (plan.precision == GP_FP32)

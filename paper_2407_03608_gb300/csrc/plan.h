@@ -77,6 +77,12 @@ struct Plan {
   size_t real_size = 8;                 // sizeof(real_t)
   // device buffers
   void* a_tensor = nullptr;             // packed A'[p][f] (real_t), p < C(C+1)/2, f over the half box
+  // memory-lean step 3 (no A'): per-dimension factors tab[j][m][lean_cp] and sqrt(v~_j)
+  bool lean = false;
+  void* lean_tab = nullptr;
+  void* lean_sqv = nullptr;
+  int lean_cp = 0;                      // channel pitch of tab (16-byte multiple)
+  int lean_J = 0;                       // quadrature nodes N_t + 1
   long long n_freq = 0;                 // frequencies in the half box
   void* grid = nullptr;                 // spreading grids (R2C input), C * max_rhs * nf^d; cells no
                                         // active tile covers stay zero from plan creation on
@@ -182,6 +188,12 @@ void build_spread2d_tiles(Plan& plan, const std::vector<int>& bstart);
 void launch_spread2d(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st);
 // Steps (2b)+(3)+(4a): deconvolve, apply A', zero outside the mode box (in spec).
 void launch_diag(Plan& plan, int R, cudaStream_t st);
+// Memory-lean step 3 (step3_lean.cu): the same map from the per-dimension factors,
+// for the transposed (tr3) and the full-grid layouts.
+int lean_channel_pitch(int C, size_t rs);
+size_t lean_smem_bytes(const Plan& plan);
+void build_lean_tables(Plan& plan);
+void launch_step3_lean(Plan& plan, int R, cudaStream_t st);
 // Steps (4b)+(5): interpolate at the points of ps and combine channels:
 // out[i] = sum_k w_k(x_i) beta_k(x_i) + shift * alpha_sorted[i] (alpha may be null).
 void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, double shift, double* out_sorted,
