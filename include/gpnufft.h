@@ -112,6 +112,14 @@ typedef struct gp_plan_opts {
                                alternative to storing A; about 4.5 C (N_t+1)
                                multiply-adds per frequency.  Not with transform 2
                                (GP_EUNSUPPORTED).                                        */
+  int diag_correct;       /* 1: add the exact diagonal defect, out_i += (K_ii - K~_ii) alpha_i
+                             with K_ii = w_i^2 (4 pi sigma_i^2)^(-d/2) (Eq. nonstat2 at x = y)
+                             and K~_ii = sum_kl w_k(x_i) w_l(x_i) sum_n A_kl[n] (Eq. Ktilde at
+                             x = y).  An extension, not in the paper: it removes the part of
+                             the truncation error that sits on the diagonal, the largest for
+                             small nu (the cusp of phi at r = 0).  Off-diagonal entries are
+                             K~'s.  Applies to matvecs and solves on the plan's own points,
+                             not to posterior means.  0 (default): K~ as in the paper.  */
 } gp_plan_opts;
 
 typedef struct gp_plan_info {
@@ -129,6 +137,7 @@ typedef struct gp_plan_info {
   long long bytes_resident;                /* device bytes the plan holds                 */
   int max_rhs;
   int step3;                               /* step-3 form in use: 1 tensor, 2 memory-lean */
+  int diag_correct;                        /* 1 when the diagonal defect is added         */
 } gp_plan_info;
 
 /* Fill opts with the defaults (all zero except max_rhs = 1). */

@@ -46,7 +46,8 @@ class gp_plan_opts(ctypes.Structure):
                 ("nufft_tol", ctypes.c_double), ("upsampfac", ctypes.c_double),
                 ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
                 ("nf", ctypes.c_longlong), ("tile", ctypes.c_int), ("transform", ctypes.c_int),
-                ("max_rhs", ctypes.c_int), ("max_bytes", ctypes.c_longlong), ("step3", ctypes.c_int)]
+                ("max_rhs", ctypes.c_int), ("max_bytes", ctypes.c_longlong), ("step3", ctypes.c_int),
+                ("diag_correct", ctypes.c_int)]
 
 
 class gp_plan_info(ctypes.Structure):
@@ -61,7 +62,8 @@ class gp_plan_info(ctypes.Structure):
                 ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
                 ("est_err_t", ctypes.c_double), ("est_err_sigma", ctypes.c_double),
                 ("est_err_trunc", ctypes.c_double), ("est_err_alias", ctypes.c_double),
-                ("bytes_resident", ctypes.c_longlong), ("max_rhs", ctypes.c_int), ("step3", ctypes.c_int)]
+                ("bytes_resident", ctypes.c_longlong), ("max_rhs", ctypes.c_int), ("step3", ctypes.c_int),
+                ("diag_correct", ctypes.c_int)]
 
     def as_dict(self):
         out = {}

@@ -411,6 +411,8 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
 
   std::vector<int> bstart;
   build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
+  GPN_CHECK(o.diag_correct == 0 || o.diag_correct == 1, GP_EINVAL, "diag_correct must be 0 or 1");
+  if (o.diag_correct) build_diag_correction(*plan, w, sig, st);
   build_active_tiles(*plan, bstart);
   if (spread2d_supported(*plan)) build_spread2d_tiles(*plan, bstart);
   if (plan->lean) {
@@ -505,7 +507,8 @@ void check_same_hyper(const Plan& a, const Plan& b) {
   const Hyper &x = a.h, &y = b.h;
   bool same = a.N == b.N && x.d == y.d && x.family == y.family && x.n_t == y.n_t && x.t_min == y.t_min &&
               x.t_max == y.t_max && x.n_sigma == y.n_sigma && x.sig_lo == y.sig_lo && x.sig_hi == y.sig_hi &&
-              x.M == y.M && x.dw == y.dw && (x.family == GP_SE || x.nu == y.nu);
+              x.M == y.M && x.dw == y.dw && (x.family == GP_SE || x.nu == y.nu) &&
+              (a.dcorr != nullptr) == (b.dcorr != nullptr);
   GPN_CHECK(same, GP_EINVAL, "plan_lo and plan_hi must share points and hyperparameters");
 }
 
@@ -797,6 +800,7 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->bytes_resident = p->bytes;
     info->max_rhs = p->max_rhs;
     info->step3 = p->lean ? 2 : 1;
+    info->diag_correct = p->dcorr ? 1 : 0;
     return GP_OK;
   });
 }

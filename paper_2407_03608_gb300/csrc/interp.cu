@@ -47,6 +47,7 @@ struct InterpArgs {
   unsigned box_bytes;    // bytes of one TMA box
   const double* alpha;   // sorted order (may be null)
   double shift;
+  const double* dcorr;   // per-point addition to the shift (sorted order, may be null)
   double* out;           // sorted order, N x R
   int* status;
 };
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
         for (int k = 0; k < CMAX; ++k)
           if (k < ncur) res += (double)a.wk[(size_t)p * C + c0 + k] * (double)acc[k];
         if (c0 == 0) {
-          if (alpha_r) res += a.shift * alpha_r[p];
+          if (alpha_r) res += (a.dcorr ? a.shift + a.dcorr[p] : a.shift) * alpha_r[p];
           out_r[p] = res;
         } else {
           out_r[p] += res;
@@ -278,6 +279,7 @@ void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, dou
   a.box_bytes = (unsigned)(interp_stage_bytes(g.d, g.tile, g.width, sizeof(T)) * a.cc);
   a.alpha = alpha_sorted;
   a.shift = shift;
+  a.dcorr = (&ps == &plan.pts) ? plan.dcorr : nullptr;
   a.out = out_sorted;
   a.status = plan.dev_status;
   // a TMA tile copy must start on a 16-byte boundary along x (x = bin * tile)

@@ -83,6 +83,7 @@ struct Plan {
   void* lean_sqv = nullptr;
   int lean_cp = 0;                      // channel pitch of tab (16-byte multiple)
   int lean_J = 0;                       // quadrature nodes N_t + 1
+  double* dcorr = nullptr;              // diagonal defect K_ii - K~_ii (sorted order), null when off
   long long n_freq = 0;                 // frequencies in the half box
   void* grid = nullptr;                 // spreading grids (R2C input), C * max_rhs * nf^d; cells no
                                         // active tile covers stay zero from plan creation on
@@ -188,6 +189,8 @@ void build_spread2d_tiles(Plan& plan, const std::vector<int>& bstart);
 void launch_spread2d(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st);
 // Steps (2b)+(3)+(4a): deconvolve, apply A', zero outside the mode box (in spec).
 void launch_diag(Plan& plan, int R, cudaStream_t st);
+// Exact diagonal correction: plan.dcorr[p] = K_pp - K~_pp (points.cu).
+void build_diag_correction(Plan& plan, const double* w_dev, const double* sig_dev, cudaStream_t st);
 // Memory-lean step 3 (step3_lean.cu): the same map from the per-dimension factors,
 // for the transposed (tr3) and the full-grid layouts.
 int lean_channel_pitch(int C, size_t rs);
@@ -195,7 +198,8 @@ size_t lean_smem_bytes(const Plan& plan);
 void build_lean_tables(Plan& plan);
 void launch_step3_lean(Plan& plan, int R, cudaStream_t st);
 // Steps (4b)+(5): interpolate at the points of ps and combine channels:
-// out[i] = sum_k w_k(x_i) beta_k(x_i) + shift * alpha_sorted[i] (alpha may be null).
+// out[i] = sum_k w_k(x_i) beta_k(x_i) + (shift + dcorr_i) * alpha_sorted[i] (alpha may be
+// null; dcorr_i, the plan's diagonal defect, only for the plan's own points when on).
 void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, double shift, double* out_sorted,
                    int R, cudaStream_t st);
 

@@ -11,6 +11,7 @@ namespace gpn {
 
 namespace {
 
+constexpr double kPi = 3.14159265358979323846264338327950;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 __global__ void k_fields_to_paper(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ w,
@@ -137,6 +138,41 @@ struct ChebArgs {
   int d;
 };
 
+// w_k(x) = w (2 pi sigma^2)^(-d/2) P_k(sigma), P_k by the barycentric formula on the
+// Chebyshev-Lobatto nodes (weights (-1)^k, halved at both ends); exact at a node.
+__device__ void cheb_weights(double w, double s, const ChebArgs& cb, double* out) {
+  const double pre = w * pow(kTwoPi * s * s, -0.5 * cb.d);
+  int hit = -1;
+  for (int k = 0; k < cb.C; ++k)
+    if (s == cb.nodes[k]) hit = k;
+  if (hit >= 0 || cb.C == 1) {
+    for (int k = 0; k < cb.C; ++k) out[k] = (k == hit || cb.C == 1) ? pre : 0.0;
+    return;
+  }
+  double den = 0.0;
+  for (int k = 0; k < cb.C; ++k) den += cb.bary[k] / (s - cb.nodes[k]);
+  for (int k = 0; k < cb.C; ++k) out[k] = pre * (cb.bary[k] / (s - cb.nodes[k])) / den;
+}
+
+// Diagonal defect K_ii - K~_ii per sorted point (see build_diag_correction).
+__global__ void k_diag_defect(const int* __restrict__ perm, long long n, const double* __restrict__ w,
+                              const double* __restrict__ sig, ChebArgs cb, const double* __restrict__ S,
+                              double* __restrict__ out) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const long long i = perm[p];
+  const double s = sig[i];
+  double wk[kMaxChannels];
+  cheb_weights(w[i], s, cb, wk);
+  double q = 0.0;
+  for (int k = 0; k < cb.C; ++k) {
+    double row = 0.0;
+    for (int l = 0; l < cb.C; ++l) row += S[k * cb.C + l] * wk[l];
+    q += wk[k] * row;
+  }
+  out[p] = w[i] * w[i] * pow(2.0 * kTwoPi * s * s, -0.5 * cb.d) - q;
+}
+
 template <typename T>
 __global__ void k_gather_points(const int* __restrict__ perm, long long n, int d, const int* __restrict__ l0_in,
                                 const double* __restrict__ xi_in, int* c0, int* c1, int* c2, T* x0, T* x1, T* x2,
@@ -151,25 +187,12 @@ __global__ void k_gather_points(const int* __restrict__ perm, long long n, int d
     cs[a][p] = l0_in[a * n + i];
     xs[a][p] = (T)xi_in[a * n + i];
   }
-  // w_k = w (2 pi sigma^2)^(-d/2) P_k(sigma), P_k by the barycentric formula on the
-  // Chebyshev-Lobatto nodes (weights (-1)^k, halved at both ends).
-  double s = sig[i];
-  double pre = w[i] * pow(kTwoPi * s * s, -0.5 * d);
-  int hit = -1;
-  for (int k = 0; k < cb.C; ++k)
-    if (s == cb.nodes[k]) hit = k;
-  if (hit >= 0 || cb.C == 1) {
-    for (int k = 0; k < cb.C; ++k) wk[p * cb.C + k] = (T)((k == hit || cb.C == 1) ? pre : 0.0);
-    wabs[p] = (float)fabs(pre);
-    return;
-  }
-  double den = 0.0;
-  for (int k = 0; k < cb.C; ++k) den += cb.bary[k] / (s - cb.nodes[k]);
+  double v[kMaxChannels];
+  cheb_weights(w[i], sig[i], cb, v);
   double m = 0.0;
   for (int k = 0; k < cb.C; ++k) {
-    const double v = pre * (cb.bary[k] / (s - cb.nodes[k])) / den;
-    wk[p * cb.C + k] = (T)v;
-    m = fmax(m, fabs(v));
+    wk[p * cb.C + k] = (T)v[k];
+    m = fmax(m, fabs(v[k]));
   }
   wabs[p] = (float)m;
 }
@@ -349,6 +372,53 @@ void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double*
   if (!act.empty())
     GPN_CUDA(cudaMemcpy(ps.active_bins, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice));
   if (bin_start_host) bin_start_host->swap(hs);
+}
+
+// Exact diagonal correction (an extension for small nu): defect_i = K_ii - K~_ii with
+//   K_ii = w_i^2 (4 pi sigma_i^2)^(-d/2)                    Eq. (nonstat2) at x = y
+//   K~_ii = sum_kl w_k(x_i) w_l(x_i) S_kl,  S = sum_{n in {-M..M}^d} A[n]   Eq. (Ktilde) at x = y
+// A[n] = sum_j v~_j G^_kj[n] G^_lj[n] (Remark rem:step3, without the NUFFT deconvolution)
+// is a product over dimensions, so S_kl = sum_j v~_j (sum_{|m|<=M} e_kj(m) e_lj(m))^d with
+// e_kj(m) = sqrt(2 pi) sigma_k chi_j exp(-2 pi^2 (sigma_k chi_j dw m)^2).  The defect is
+// stored in sorted order (float64) and added to the matvec's shift term.
+void build_diag_correction(Plan& plan, const double* w_dev, const double* sig_dev, cudaStream_t st) {
+  const Hyper& h = plan.h;
+  const Tables& tb = plan.tb;
+  const int C = plan.geom.C, J = (int)tb.vt.size(), d = h.d;
+  std::vector<double> S((size_t)C * C, 0.0);
+  for (int j = 0; j < J; ++j)
+    for (int k = 0; k < C; ++k)
+      for (int l = k; l < C; ++l) {
+        double s1 = 0.0;
+        for (long long m = h.M; m >= 0; --m) {   // small terms first
+          const double ak = tb.nodes[k] * tb.chi[j] * h.dw * (double)m;
+          const double al = tb.nodes[l] * tb.chi[j] * h.dw * (double)m;
+          const double pk = std::sqrt(2.0 * kPi) * tb.nodes[k] * tb.chi[j] * std::exp(-2.0 * kPi * kPi * ak * ak);
+          const double pl = std::sqrt(2.0 * kPi) * tb.nodes[l] * tb.chi[j] * std::exp(-2.0 * kPi * kPi * al * al);
+          s1 += (m == 0 ? 1.0 : 2.0) * pk * pl;
+        }
+        const double v = tb.vt[j] * std::pow(s1, d);
+        S[(size_t)k * C + l] += v;
+        if (l != k) S[(size_t)l * C + k] += v;
+      }
+  plan.dcorr = (double*)plan.alloc(sizeof(double) * (size_t)std::max<long long>(plan.N, 1));
+  double* Sd = nullptr;
+  GPN_CUDA(cudaMalloc(&Sd, sizeof(double) * S.size()));
+  cudaError_t e = cudaMemcpyAsync(Sd, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && plan.N > 0) {
+    ChebArgs cb{};
+    cb.C = C;
+    cb.d = d;
+    for (int k = 0; k < C; ++k) {
+      cb.nodes[k] = tb.nodes[k];
+      cb.bary[k] = tb.bary[k];
+    }
+    k_diag_defect<<<blocks_for(plan.N, 256), 256, 0, st>>>(plan.pts.perm, plan.N, w_dev, sig_dev, cb, Sd, plan.dcorr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(Sd);
+  GPN_CUDA(e);
 }
 
 }  // namespace gpn
