@@ -120,6 +120,13 @@ typedef struct gp_plan_opts {
                              small nu (the cusp of phi at r = 0).  Off-diagonal entries are
                              K~'s.  Applies to matvecs and solves on the plan's own points,
                              not to posterior means.  0 (default): K~ as in the paper.  */
+  int autotune;           /* 0 (default): the spread/interp tile from the shared-memory
+                             heuristic.  k in 1..8: also build plans with up to k other
+                             tiles the kernels accept (gp_tile_candidates, nearest to the
+                             heuristic's first), time R = 1 matvecs of each with CUDA events
+                             on the caller's stream, keep the fastest.  Tiles and bins are
+                             the same size, so this tunes both.  Holds two plans at a time;
+                             ignored when GP_SET_TILE is set.                            */
 } gp_plan_opts;
 
 typedef struct gp_plan_info {
@@ -138,7 +145,15 @@ typedef struct gp_plan_info {
   int max_rhs;
   int step3;                               /* step-3 form in use: 1 tensor, 2 memory-lean */
   int diag_correct;                        /* 1 when the diagonal defect is added         */
+  int tuned;                               /* plans the autotuner timed (0: not tuned)    */
+  double tune_ms;                          /* this plan's matvec time in the autotuner    */
 } gp_plan_info;
+
+/* The autotuner's search space (host only, no GPU needed): every spread/interp tile
+ * edge the kernels accept for d, n_channels = N_sigma + 1, precision (GP_FP32 or
+ * GP_FP64) and the spreading kernel width, largest first.  Writes at most max_tiles
+ * of them to tiles and returns how many there are (or a negative gp_status). */
+int gp_tile_candidates(int d, int n_channels, int precision, int width, int* tiles, int max_tiles);
 
 /* Fill opts with the defaults (all zero except max_rhs = 1). */
 void gp_plan_opts_default(gp_plan_opts* opts);

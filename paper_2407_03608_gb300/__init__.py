@@ -76,7 +76,8 @@ class Plan:
                   "n_sigma": abi.GP_SET_NSIGMA, "sigma_lo": abi.GP_SET_SIGMA_RANGE, "sigma_hi": abi.GP_SET_SIGMA_RANGE,
                   "M": abi.GP_SET_M, "dw": abi.GP_SET_DW, "nufft_tol": abi.GP_SET_NUFFT,
                   "upsampfac": abi.GP_SET_NUFFT, "box_lo": abi.GP_SET_BOX, "box_hi": abi.GP_SET_BOX,
-                  "nf": abi.GP_SET_NF, "tile": abi.GP_SET_TILE, "max_bytes": 0, "transform": 0, "step3": 0, "diag_correct": 0}
+                  "nf": abi.GP_SET_NF, "tile": abi.GP_SET_TILE, "max_bytes": 0, "transform": 0, "step3": 0, "diag_correct": 0,
+                  "autotune": 0}
         for k, v in overrides.items():
             if k not in keymap:
                 raise TypeError("unknown plan option %r" % k)

@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "GP_OK", -1: "GP_EINVAL", -2: "GP_ENOMEM", -3: "GP_ECUDA", -4
 #: every symbol include/gpnufft.h declares
 EXPORTED = ["gp_plan_opts_default", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined",
             "gp_posterior_mean", "gp_posterior_mean_noalloc", "gp_posterior_variance", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
-            "gp_version"]
+            "gp_version", "gp_tile_candidates"]
 
 
 class gp_plan_opts(ctypes.Structure):
@@ -47,7 +47,7 @@ class gp_plan_opts(ctypes.Structure):
                 ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
                 ("nf", ctypes.c_longlong), ("tile", ctypes.c_int), ("transform", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("max_bytes", ctypes.c_longlong), ("step3", ctypes.c_int),
-                ("diag_correct", ctypes.c_int)]
+                ("diag_correct", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class gp_plan_info(ctypes.Structure):
@@ -63,7 +63,7 @@ class gp_plan_info(ctypes.Structure):
                 ("est_err_t", ctypes.c_double), ("est_err_sigma", ctypes.c_double),
                 ("est_err_trunc", ctypes.c_double), ("est_err_alias", ctypes.c_double),
                 ("bytes_resident", ctypes.c_longlong), ("max_rhs", ctypes.c_int), ("step3", ctypes.c_int),
-                ("diag_correct", ctypes.c_int)]
+                ("diag_correct", ctypes.c_int), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -110,6 +110,9 @@ def _load():
     lib.gp_last_error.restype = ctypes.c_char_p
     lib.gp_version.argtypes = []
     lib.gp_version.restype = ctypes.c_char_p
+    lib.gp_tile_candidates.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    lib.gp_tile_candidates.restype = ctypes.c_int
     return lib
 
 
@@ -272,6 +275,14 @@ def gp_destroy(plan):
 
 def gp_version() -> str:
     return LIB.gp_version().decode()
+
+
+def gp_tile_candidates(d: int, n_channels: int, precision: int, width: int) -> list:
+    """The autotuner's search space: tile edges the kernels accept, largest first (no GPU)."""
+    buf = (ctypes.c_int * 32)()
+    n = LIB.gp_tile_candidates(d, n_channels, precision, width, buf, 32)
+    check(min(n, 0))
+    return [buf[i] for i in range(min(n, 32))]
 
 
 def _is_writable_target(orig, keep):

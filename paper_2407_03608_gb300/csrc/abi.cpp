@@ -83,26 +83,54 @@ void* tmp_alloc_cb(void* ctx, size_t bytes) {
 // that covers a point's support in two bins (tile >= width - 1).  When no tile holds
 // every channel, the largest holding one channel: the spreading then runs in channel
 // chunks.
+const int kTiles1[] = {4096, 2048, 1024, 512, 256, 128, 64, 32, 16};
+const int kTiles2[] = {64, 48, 32, 24, 16, 12, 8};
+const int kTiles3[] = {16, 12, 10, 8, 6, 4};
+
+// A tile the kernels accept: no smaller than the support, 16-byte TMA boxes along x for
+// d >= 2 (staged from x = bin * tile), a staged interp block that fits, and a spreading
+// tile of `chans` channels within `budget` bytes of shared memory.
+bool tile_ok(int d, int t, int chans, size_t rs, int width, size_t budget) {
+  if (t < width - 1) return false;
+  if (d >= 2 && (t * rs) % 16 != 0) return false;
+  return spread_smem_bytes(d, t, chans, rs, width) <= budget && interp_stage_bytes(d, t, width, rs) <= kInterpSmemMax;
+}
+
 int choose_tile(int d, int C, size_t rs, int width) {
-  static const int c1[] = {4096, 2048, 1024, 512, 256, 128, 64, 32, 16};
-  static const int c2[] = {64, 48, 32, 24, 16, 12, 8};
-  static const int c3[] = {16, 12, 10, 8, 6, 4};
-  const int* c = d == 1 ? c1 : (d == 2 ? c2 : c3);
+  const int* c = d == 1 ? kTiles1 : (d == 2 ? kTiles2 : kTiles3);
   int nc = d == 1 ? 9 : (d == 2 ? 7 : 6);
   for (int chans : {C, 1}) {
     for (size_t budget : {size_t(64) << 10, kSpreadSmemMax}) {
-      for (int i = 0; i < nc; ++i) {
-        if (c[i] < width - 1) continue;
-        // d >= 2 stages interp tiles with TMA from x = bin * tile: 16-byte aligned only
-        // when tile * rs is a multiple of 16
-        if (d >= 2 && (c[i] * rs) % 16 != 0) continue;
-        if (spread_smem_bytes(d, c[i], chans, rs, width) <= budget &&
-            interp_stage_bytes(d, c[i], width, rs) <= kInterpSmemMax)
-          return c[i];
-      }
+      for (int i = 0; i < nc; ++i)
+        if (tile_ok(d, c[i], chans, rs, width, budget)) return c[i];
     }
   }
   fail(GP_EUNSUPPORTED, "no spreading tile fits in shared memory for this kernel width");
+}
+
+// The autotuner's search space: every tile the kernels accept for (d, C, rs, width),
+// largest first (channel chunks allowed, as for the heuristic's last resort).
+std::vector<int> tile_candidates(int d, int C, size_t rs, int width) {
+  const int* c = d == 1 ? kTiles1 : (d == 2 ? kTiles2 : kTiles3);
+  int nc = d == 1 ? 9 : (d == 2 ? 7 : 6);
+  std::vector<int> out;
+  for (int i = 0; i < nc; ++i)
+    if (tile_ok(d, c[i], C, rs, width, kSpreadSmemMax) || tile_ok(d, c[i], 1, rs, width, kSpreadSmemMax))
+      out.push_back(c[i]);
+  return out;
+}
+
+// The autotuner's trial order around the heuristic's tile t0: t0's neighbours in the
+// candidate list, nearest first, at most `max_trials` of them.
+std::vector<int> tile_trials(const std::vector<int>& cands, int t0, int max_trials) {
+  std::vector<int> rest;
+  for (int t : cands)
+    if (t != t0) rest.push_back(t);
+  std::stable_sort(rest.begin(), rest.end(), [t0](int a, int b) {
+    return std::fabs(std::log((double)a / t0)) < std::fabs(std::log((double)b / t0));
+  });
+  if ((int)rest.size() > max_trials) rest.resize(max_trials);
+  return rest;
 }
 
 int set_error(const Error& e) {
@@ -533,9 +561,47 @@ int gp_plan(gp_plan_t* out, const double* points, long long N, int d, const doub
     gp_plan_opts o;
     gp_plan_opts_default(&o);
     if (opts) o = *opts;
-    Plan* p = make_plan(points, N, d, field_a, field_b, nu, eps, o, (cudaStream_t)cuda_stream);
-    *out = reinterpret_cast<gp_plan_t>(p);
+    GPN_CHECK(o.autotune >= 0 && o.autotune <= 8, GP_EINVAL, "autotune must be in 0..8");
+    const cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::unique_ptr<Plan> best(make_plan(points, N, d, field_a, field_b, nu, eps, o, st));
+    if (o.autotune > 0 && !(o.set & GP_SET_TILE)) {
+      // time the heuristic's plan and up to `autotune` alternatives with other tiles;
+      // keep the fastest (two plans are held at a time)
+      const Hyper& h = best->h;
+      const auto trials = tile_trials(tile_candidates(h.d, best->geom.C, best->real_size, h.width), h.tile, o.autotune);
+      best->tune_ms = time_matvecs(*best, st);
+      for (int t : trials) {
+        gp_plan_opts o2 = o;
+        o2.set |= GP_SET_TILE;
+        o2.tile = t;
+        o2.autotune = 0;
+        std::unique_ptr<Plan> cand;
+        try {
+          cand.reset(make_plan(points, N, d, field_a, field_b, nu, eps, o2, st));
+        } catch (const Error&) {
+          cudaGetLastError();   // clear a failed allocation's error state
+          continue;             // this tile does not fit (memory, shared memory): not a candidate
+        }
+        cand->tune_ms = time_matvecs(*cand, st);
+        if (cand->tune_ms < best->tune_ms) best.swap(cand);
+      }
+      best->tuned = (int)trials.size() + 1;
+    }
+    *out = reinterpret_cast<gp_plan_t>(best.release());
     return GP_OK;
+  });
+}
+
+int gp_tile_candidates(int d, int n_channels, int precision, int width, int* tiles, int max_tiles) {
+  return guarded([&]() {
+    GPN_CHECK(d >= 1 && d <= 3 && n_channels >= 1 && n_channels <= kMaxChannels && width >= 2 && width <= kMaxWidth,
+              GP_EINVAL, "bad d, n_channels or width");
+    GPN_CHECK(precision == GP_FP64 || precision == GP_FP32, GP_EINVAL, "bad precision");
+    GPN_CHECK(tiles != nullptr || max_tiles == 0, GP_EINVAL, "null output");
+    const auto c = tile_candidates(d, n_channels, precision == GP_FP32 ? 4 : 8, width);
+    const int n = std::min<int>((int)c.size(), max_tiles);
+    for (int i = 0; i < n; ++i) tiles[i] = c[i];
+    return (int)c.size();
   });
 }
 
@@ -801,6 +867,8 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->max_rhs = p->max_rhs;
     info->step3 = p->lean ? 2 : 1;
     info->diag_correct = p->dcorr ? 1 : 0;
+    info->tuned = p->tuned;
+    info->tune_ms = p->tune_ms;
     return GP_OK;
   });
 }

@@ -195,4 +195,29 @@ void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, i
   }
 }
 
+double time_matvecs(Plan& plan, cudaStream_t st) {
+  // every byte 0x3F: each alpha_i is the same finite double (about 4.8e-4); the kernels'
+  // work does not depend on the values
+  GPN_CUDA(cudaMemsetAsync(plan.vec_a, 0x3F, sizeof(double) * (size_t)plan.N, st));
+  for (int i = 0; i < 2; ++i) matvec_sorted(plan, plan.vec_a, plan.vec_b, 1, 0.0, st);
+  cudaEvent_t e0, e1;
+  GPN_CUDA(cudaEventCreate(&e0));
+  GPN_CUDA(cudaEventCreate(&e1));
+  constexpr int kReps = 3;
+  cudaError_t e = cudaEventRecord(e0, st);
+  for (int i = 0; i < kReps && e == cudaSuccess; ++i) {
+    matvec_sorted(plan, plan.vec_a, plan.vec_b, 1, 0.0, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GPN_CUDA(e);
+  check_device_status(plan, st);
+  return ms / kReps;
+}
+
 }  // namespace gpn

@@ -84,6 +84,8 @@ struct Plan {
   int lean_cp = 0;                      // channel pitch of tab (16-byte multiple)
   int lean_J = 0;                       // quadrature nodes N_t + 1
   double* dcorr = nullptr;              // diagonal defect K_ii - K~_ii (sorted order), null when off
+  int tuned = 0;                        // plans timed by the tile autotuner (0: not tuned)
+  double tune_ms = 0.0;                 // this plan's matvec time in the autotuner
   long long n_freq = 0;                 // frequencies in the half box
   void* grid = nullptr;                 // spreading grids (R2C input), C * max_rhs * nf^d; cells no
                                         // active tile covers stay zero from plan creation on
@@ -235,6 +237,8 @@ void tr3_inverse(Plan& plan, int R, cudaStream_t st);
 
 // Full matvec in sorted order: out = (K~ + shift I) alpha.
 void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st);
+// Milliseconds per matvec (R = 1, CUDA events, after two untimed ones) on a fixed input.
+double time_matvecs(Plan& plan, cudaStream_t st);
 
 // Permutations between caller order and sorted order (N x R column-major).
 void gather_sorted(const PointSet& ps, const double* src, double* dst, int R, cudaStream_t st);
