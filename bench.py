@@ -456,11 +456,21 @@ def measure_config3(dev, steps=3):
     abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, 1)
     ms = _events_ms(lambda: abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, steps), 1) / steps
     i = plan.info
+    opts = plan.matched_opts()
     plan.close()
+    # the same plan with the memory-lean step 3 (no A' tensor)
+    lean = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
+                    torch.from_numpy(w.l).to(dev), nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, step3=2, **opts)
+    abi.gp_cg_solve(lean.handle, y, x, 1, w.eta ** 2, 1e-30, 1)
+    ms_lean = _events_ms(lambda: abi.gp_cg_solve(lean.handle, y, x, 1, w.eta ** 2, 1e-30, steps), 1) / steps
+    lean_bytes = int(lean.info["bytes_resident"])
+    lean.close()
     return {"workload": w.name, "precision": "fp32 (f64 CG)", "ms_per_step": round(ms, 3),
             "value": round(w.N / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "plan_seconds": round(plan_s, 3),
             "nf": i["nf"], "M": i["M"], "n_sigma": i["n_sigma"], "kernel_width": i["kernel_width"],
-            "bytes_resident": int(i["bytes_resident"])}
+            "bytes_resident": int(i["bytes_resident"]),
+            "memory_lean_step3": {"ms_per_step": round(ms_lean, 3), "value": round(w.N / (ms_lean * 1e-3) / 1e6, 3),
+                                  "bytes_resident": lean_bytes}}
 
 
 def measure_serving(n_requests):

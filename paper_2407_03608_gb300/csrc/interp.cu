@@ -10,8 +10,11 @@
 // each point:
 //   d = 1: one lane per point;  d = 2: one lane per support row (width lanes);
 //   d = 3: one warp per point, lanes over the width^2 pencils.
-// Each lane accumulates its channels in registers, the group is reduced with
-// shuffles, and the group leader applies the Chebyshev weights w_k(x_i) in float64.
+// Each lane accumulates its channels in registers.  d = 2: the lanes of a point write
+// their per-row sums to shared memory and lane k of the point adds up channel k's rows
+// (a transpose instead of one shuffle tree per channel), forms w_k(x_i) beta_k in FP32 and
+// the group sums the products in float64.  d = 1, 3: the group is reduced with shuffles
+// and the group leader applies w_k(x_i) in float64.
 // The mbarrier wait is bounded: when it runs out the CTA records a timeout in the
 // plan's device status word and returns.
 #include <algorithm>
@@ -52,11 +55,21 @@ struct InterpArgs {
   int* status;
 };
 
-template <typename T, int D, int CMAX, bool TMA>
+// d = 2 channel-sum transpose: per warp, 32 lanes x (CMAX | 1) values (odd row pitch)
+template <typename T, int D, int CMAX>
+__host__ __device__ constexpr bool use_transpose() { return D == 2 && CMAX <= 16; }
+template <typename T, int D, int CMAX>
+__host__ __device__ constexpr size_t transpose_bytes() { return use_transpose<T, D, CMAX>() ? 8 * 32 * (CMAX | 1) * sizeof(T) : 0; }
+
+// EXACT: every channel chunk holds exactly CMAX channels (C = cc = CMAX), so the
+// channel loops run without guards.
+template <typename T, int D, int CMAX, bool TMA, bool EXACT>
 __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
   T* st = reinterpret_cast<T*>(smem_raw + 128);
+  // after the staged block (box_bytes, a multiple of 16)
+  T* s_red = reinterpret_cast<T*>(smem_raw + 128 + a.box_bytes);
   const int bin = a.bins[blockIdx.x];
   const int p0 = a.bin_start[bin], p1 = a.bin_start[bin + 1];
   const int npts = p1 - p0;
@@ -160,7 +173,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
             const T wgt = es_psi<T>((T)i - x[0], a.beta, a.inv_halfw);
 #pragma unroll
             for (int k = 0; k < CMAX; ++k)
-              if (k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+              if (EXACT || k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
           }
         }
       } else {
@@ -187,18 +200,49 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
             off = off * E + l0[q] + iq[q];
           }
           const T* rowp = st + (size_t)off * EP + l0[D - 1];
+#pragma unroll 3
           for (int i = 0; i < W; ++i) {
             const T wgt = plead * __shfl_sync(0xffffffffu, pq[D - 1], src + i);
             if (valid) {
 #pragma unroll
               for (int k = 0; k < CMAX; ++k)
-                if (k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+                if (EXACT || k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
             }
           }
         }
       }
       // reduce within the point's lane group
-      if (kGroup == 32) {
+      if constexpr (use_transpose<T, D, CMAX>()) {
+        constexpr int RP = CMAX | 1;   // odd pitch: the 32 lanes write to 32 banks
+        T* red = s_red + (size_t)warp * 32 * RP;
+#pragma unroll
+        for (int k = 0; k < CMAX; ++k)
+          if (EXACT || k < ncur) red[lane * RP + k] = acc[k];
+        __syncwarp();
+        double part = 0.0;
+        if (grp < ppw) {   // lanes past the last full group hold no point
+          for (int k = gl; k < ncur; k += Gs) {
+            T sum = T(0);
+            for (int row = 0; row < Gs; ++row) sum += red[(grp * Gs + row) * RP + k];
+            part += (double)(a.wk[(size_t)p * C + c0 + k] * sum);
+          }
+        }
+        __syncwarp();   // red is rewritten by the next point batch
+        for (int o = 1; o < Gs; o <<= 1) {
+          const double v = __shfl_down_sync(0xffffffffu, part, o);
+          if (gl + o < Gs) part += v;
+        }
+        if (active && gl == 0) {
+          double res = part;
+          if (c0 == 0) {
+            if (alpha_r) res += (a.dcorr ? a.shift + a.dcorr[p] : a.shift) * alpha_r[p];
+            out_r[p] = res;
+          } else {
+            out_r[p] += res;
+          }
+        }
+        continue;
+      } else if (kGroup == 32) {
 #pragma unroll
         for (int k = 0; k < CMAX; ++k) {
           if (k < ncur) {
@@ -233,15 +277,26 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
   }
 }
 
-template <typename T, int D, int CMAX, bool TMA>
-void launch(const InterpArgs<T>& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
-  GPN_CUDA(
-      cudaFuncSetAttribute(k_interp<T, D, CMAX, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_interp<T, D, CMAX, TMA><<<grid, 256, smem, st>>>(a, tm);
+template <typename T, int D, int CMAX, bool TMA, bool EXACT = false>
+void launch(const InterpArgs<T>& a, const CUtensorMap& tm, dim3 grid, size_t smem0, cudaStream_t st) {
+  const size_t smem = smem0 + transpose_bytes<T, D, CMAX>();
+  GPN_CUDA(cudaFuncSetAttribute(k_interp<T, D, CMAX, TMA, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  k_interp<T, D, CMAX, TMA, EXACT><<<grid, 256, smem, st>>>(a, tm);
+}
+
+// d = 2 with all channels in one chunk and C <= 16: the exact channel count
+template <typename T, int NC>
+void launch_exact2(const InterpArgs<T>& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
+  if constexpr (NC <= 16) {
+    if (a.C == NC) return launch<T, 2, NC, true, true>(a, tm, grid, smem, st);
+    launch_exact2<T, NC + 1>(a, tm, grid, smem, st);
+  }
 }
 
 template <typename T, int D, bool TMA>
 void launch_c(const InterpArgs<T>& a, const CUtensorMap& tm, dim3 grid, size_t smem, cudaStream_t st) {
+  if (D == 2 && a.cc == a.C && a.C <= 16) return launch_exact2<T, 1>(a, tm, grid, smem, st);
   switch (cmax_bucket(a.cc)) {
     case 8: launch<T, D, 8, TMA>(a, tm, grid, smem, st); break;
     case 12: launch<T, D, 12, TMA>(a, tm, grid, smem, st); break;
