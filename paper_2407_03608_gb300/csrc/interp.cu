@@ -103,9 +103,24 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
   if (TMA && threadIdx.x == 0) mbar_init(bar, 1);
   unsigned phase = 0;
 
+  // a batch's per-point data (first support cell relative to the block, offset xi);
+  // the next batch's is loaded while the current one is processed, the first one while
+  // the staging copy is in flight
+  auto load_pt = [&](int pb_, int (&L)[kMaxDim], T (&X)[kMaxDim]) {
+    const int pi_ = pb_ + grp;
+    const int p_ = p0 + ((grp < ppw && pi_ < npts) ? pi_ : 0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      L[q] = a.cell0[q][p_] - base[q];
+      X[q] = a.xi[q][p_];
+    }
+  };
   for (int c0 = 0; c0 < C; c0 += a.cc) {
     const int ncur = min(a.cc, C - c0);
     __syncthreads();  // the previous chunk has been read (and the barrier initialised)
+    int nl0[kMaxDim];
+    T nx[kMaxDim];
+    load_pt(warp * ppw, nl0, nx);
     if (TMA) {
       if (threadIdx.x == 0) {
         mbar_expect_tx(bar, a.box_bytes);
@@ -163,8 +178,17 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
       T x[kMaxDim];
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        l0[q] = a.cell0[q][p] - base[q];
-        x[q] = a.xi[q][p];
+        l0[q] = nl0[q];
+        x[q] = nx[q];
+      }
+      if (pb + nwarps * ppw < npts) load_pt(pb + nwarps * ppw, nl0, nx);
+      // the epilogue's own inputs, loaded before the accumulation so their latency is hidden
+      T wk_gl = T(0);
+      double shift_al = 0.0;
+      if constexpr (use_transpose<T, D, CMAX>()) {
+        if (grp < ppw && gl < ncur) wk_gl = a.wk[(size_t)p * C + c0 + gl];
+        if (active && gl == 0 && c0 == 0 && alpha_r)
+          shift_al = (a.dcorr ? a.shift + a.dcorr[p] : a.shift) * alpha_r[p];
       }
       if (D == 1) {
         if (active) {
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
           for (int k = gl; k < ncur; k += Gs) {
             T sum = T(0);
             for (int row = 0; row < Gs; ++row) sum += red[(grp * Gs + row) * RP + k];
-            part += (double)(a.wk[(size_t)p * C + c0 + k] * sum);
+            part += (double)((k == gl ? wk_gl : a.wk[(size_t)p * C + c0 + k]) * sum);
           }
         }
         __syncwarp();   // red is rewritten by the next point batch
@@ -233,13 +257,10 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
           if (gl + o < Gs) part += v;
         }
         if (active && gl == 0) {
-          double res = part;
-          if (c0 == 0) {
-            if (alpha_r) res += (a.dcorr ? a.shift + a.dcorr[p] : a.shift) * alpha_r[p];
-            out_r[p] = res;
-          } else {
-            out_r[p] += res;
-          }
+          if (c0 == 0)
+            out_r[p] = part + shift_al;
+          else
+            out_r[p] += part;
         }
         continue;
       } else if (kGroup == 32) {
