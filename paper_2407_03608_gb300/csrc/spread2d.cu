@@ -18,6 +18,7 @@
 // coalesced stores.  Tiles whose candidate bins are empty are never launched; their
 // cells stay zero from plan creation on.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -32,11 +33,16 @@ constexpr int kWarps = 8;
 constexpr int kLists = kWarps * kGroups;     // (band, strip) lists
 constexpr int kSlots = 256;                  // candidates scanned per round (one per thread)
 constexpr int kMaxRanges = 8;                // bin rows a tile's candidates can come from
-constexpr int kPsiStride = 17;               // x table stride (width <= 16), odd against bank conflicts
+constexpr int kMaxW = 16;                    // widest kernel support the tables hold
 
-// The row table of a point holds psi(j - xi) at j + RPW - 1 with zeros around, so a band
-// row just outside the support reads zero without a test.
-__host__ __device__ constexpr int row_stride(int rpw) { return (16 + 2 * (rpw - 1)) | 1; }
+// Per-slot shared tables, strides odd against bank conflicts: the x table holds
+// psi(j - xi) for j < W; the row table holds psi(j - xi) at j + RPW - 1 with zeros around,
+// so a band row just outside the support reads zero without a test.
+__host__ __device__ constexpr int col_stride(int w) { return w | 1; }
+__host__ __device__ constexpr int row_stride(int w, int rpw) { return (w + 2 * (rpw - 1)) | 1; }
+// w_k alpha of a slot: NC channels padded to whole 16-byte vectors
+template <typename T>
+__host__ __device__ constexpr int wk_pitch(int nc) { return (nc + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T)); }
 
 template <typename T>
 struct Spread2Args {
@@ -65,14 +71,16 @@ struct Spread2Args {
 template <typename T, int NC, int RPW>
 __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
   constexpr int TY = kWarps * RPW;
-  constexpr int SY = row_stride(RPW);
+  constexpr int WP = wk_pitch<T>(NC);
+  constexpr int VW = (int)(16 / sizeof(T));
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int PSX = col_stride(a.width), SY = row_stride(a.width, RPW);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s_psx = reinterpret_cast<T*>(smem_raw);                    // [kSlots][kPsiStride]
-  T* s_psy = s_psx + kSlots * kPsiStride;                        // [kSlots][SY]
-  T* s_wk = s_psy + kSlots * SY;                                 // [NC][kSlots]
-  int* s_l0x = reinterpret_cast<int*>(s_wk + NC * kSlots);       // [kSlots]
-  int* s_l0y = s_l0x + kSlots;                                   // [kSlots]
-  unsigned short* s_list = reinterpret_cast<unsigned short*>(s_l0y + kSlots);  // [kLists][kSlots]
+  T* s_wk = reinterpret_cast<T*>(smem_raw);                      // [kSlots][WP]
+  int2* s_l0 = reinterpret_cast<int2*>(s_wk + kSlots * WP);      // [kSlots]: (l0y, l0x)
+  T* s_psx = reinterpret_cast<T*>(s_l0 + kSlots);                // [kSlots][PSX]
+  T* s_psy = s_psx + kSlots * PSX;                               // [kSlots][SY]
+  unsigned char* s_list = reinterpret_cast<unsigned char*>(s_psy + kSlots * SY);  // [kLists][kSlots]
   __shared__ int s_rs[kMaxRanges], s_rl[kMaxRanges], s_wcnt[kWarps];
   __shared__ int s_cnt[kLists][kWarps], s_len[kLists];
 
@@ -167,11 +175,10 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
     }
     const int slot = off + __popc(bal & lt);
     if (meets) {
-      s_l0y[slot] = l0y;
-      s_l0x[slot] = l0x;
+      s_l0[slot] = make_int2(l0y, l0x);
       const T yq = a.xiy[p], xq = a.xix[p];
       T* py = s_psy + slot * SY;
-      T* px = s_psx + slot * kPsiStride;
+      T* px = s_psx + slot * PSX;
       for (int j = 0; j < W; ++j) px[j] = es_psi<T>((T)j - xq, a.beta, a.inv_halfw);
       for (int j = 0; j < SY; ++j) {
         const int jj = j - (RPW - 1);
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
       const T amp = (T)alpha_r[p];
       const T* wkp = a.wk + (size_t)p * C;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) s_wk[k * kSlots + slot] = k < C ? wkp[k] * amp : T(0);
+      for (int k = 0; k < WP; ++k) s_wk[slot * WP + k] = k < C ? wkp[k] * amp : T(0);
     }
     __syncthreads();
     // fill the lists in candidate order
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
     for (int L = 0; L < kLists; ++L) {
       const unsigned hit = (mask >> L) & 1u;
       const unsigned bl = __ballot_sync(0xffffffffu, hit);
-      if (hit) s_list[L * kSlots + s_cnt[L][warp] + __popc(bl & lt)] = (unsigned short)slot;
+      if (hit) s_list[L * kSlots + s_cnt[L][warp] + __popc(bl & lt)] = (unsigned char)slot;
     }
     __syncthreads();
     // accumulate: group g walks the list of (its warp's band, strip g)
@@ -196,16 +203,28 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
     int steps = 0;
 #pragma unroll
     for (int q = 0; q < kGroups; ++q) steps = max(steps, s_len[warp * kGroups + q]);
-    const unsigned short* lst = s_list + my_list * kSlots;
+    const unsigned char* lst = s_list + my_list * kSlots;
     for (int j = 0; j < steps; ++j) {
       const bool valid = j < len;
       const int is = valid ? lst[j] : 0;   // slot 0 exists whenever some list is non-empty
-      const int dyo = valid ? rw0 - s_l0y[is] : 0;   // in [1 - RPW, W - 1] for list members
-      const int dx = xg - s_l0x[is];
-      const T px = (valid && (unsigned)dx < (unsigned)W) ? s_psx[is * kPsiStride + dx] : T(0);
-      T wk[NC];
+      const int2 l0 = s_l0[is];
+      const int dyo = valid ? rw0 - l0.x : 0;   // in [1 - RPW, W - 1] for list members
+      const int dx = xg - l0.y;
+      const T px = (valid && (unsigned)dx < (unsigned)W) ? s_psx[is * PSX + dx] : T(0);
+      T wk[WP];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) wk[k] = s_wk[k * kSlots + is];
+      for (int v = 0; v < WP / VW; ++v) {
+        const V u = reinterpret_cast<const V*>(s_wk + is * WP)[v];
+        if constexpr (VW == 4) {
+          wk[4 * v] = u.x;
+          wk[4 * v + 1] = u.y;
+          wk[4 * v + 2] = u.z;
+          wk[4 * v + 3] = u.w;
+        } else {
+          wk[2 * v] = u.x;
+          wk[2 * v + 1] = u.y;
+        }
+      }
       const T* pyr = s_psy + is * SY + (RPW - 1) + dyo;
 #pragma unroll
       for (int rr = 0; rr < RPW; ++rr) {
@@ -239,15 +258,15 @@ constexpr int rows_per_warp(int nc) {
   return (sizeof(T) == 8 || nc > 16) ? 2 : 4;
 }
 
-size_t smem_bytes(size_t rs, int nc, int rpw) {
-  return (size_t)kSlots *
-         ((kPsiStride + row_stride(rpw)) * rs + nc * rs + 2 * sizeof(int) + kLists * sizeof(unsigned short));
+size_t smem_bytes(size_t rs, int nc, int rpw, int w) {
+  const int wp = rs == 4 ? wk_pitch<float>(nc) : wk_pitch<double>(nc);
+  return (size_t)kSlots * ((col_stride(w) + row_stride(w, rpw)) * rs + wp * rs + sizeof(int2) + kLists);
 }
 
 template <typename T, int NC>
 void launch(const Spread2Args<T>& a, dim3 grid, cudaStream_t st) {
   constexpr int RPW = rows_per_warp<T>(NC);
-  const size_t smem = smem_bytes(sizeof(T), NC, RPW);
+  const size_t smem = smem_bytes(sizeof(T), NC, RPW, a.width);
   GPN_CUDA(cudaFuncSetAttribute(k_spread2d<T, NC, RPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_spread2d<T, NC, RPW><<<grid, kWarps * 32, smem, st>>>(a);
 }
@@ -305,11 +324,11 @@ int spread2d_rows(const Plan& plan) {
 
 bool spread2d_supported(const Plan& plan) {
   const GridGeom& g = plan.geom;
-  if (g.d != 2 || g.width > kPsiStride || g.C > kMaxChannels) return false;
+  if (g.d != 2 || g.width > kMaxW || g.C > kMaxChannels) return false;
   const int TY = spread2d_rows(plan);
   const int bin_rows = (TY + g.width - 2) / g.tile + 2;
   const int nc = reg_channels(g.C);
-  return bin_rows <= kMaxRanges && smem_bytes(plan.real_size, nc, TY / kWarps) <= 200 * 1024;
+  return bin_rows <= kMaxRanges && smem_bytes(plan.real_size, nc, TY / kWarps, g.width) <= 200 * 1024;
 }
 
 // Tiles whose candidate bins hold at least one point; the others stay zero.
