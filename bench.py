@@ -164,7 +164,7 @@ MEASURED_TRAFFIC = {
     ("d2_N1000000_clustered_matern32", "f32", 1e-06): {
         "spread": None,   # kernel changed since the capture: re-take before reporting
         "fft_fwd": (1.174e9 + 1.109e9) + (1.663e9 + 1.607e9),
-        "diag": 2.586e9 + 1.111e9,
+        "diag": None,     # kernel changed since the capture: re-take before reporting
         "fft_inv": (1.663e9 + 1.607e9) + (1.158e9 + 1.108e9),
         "interp": 1.196e9 + 0.008e9,
     },

@@ -382,6 +382,40 @@ __global__ void __launch_bounds__(128) k_diag_t(DiagTArgs<T> a) {
   const size_t off_n = (size_t)m * a.nf + (n1 == 0 ? 0 : a.nf - n1);
   const T* Am = a.A + (size_t)m * Mp + n1;
   const size_t pstride = Mp * Mp;
+  // up to 11 channels: all C(C+1)/2 entries of A' at this frequency are loaded at once,
+  // before the right-hand sides (many loads in flight; A' read once for every rhs)
+  constexpr int NP = NC * (NC + 1) / 2;
+  if constexpr (kReg && NC <= 11) {
+    T av[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) av[p] = __ldg(Am + (size_t)p * pstride);
+    for (int r = 0; r < a.R; ++r) {
+      const cpx<T>* Yr = a.Y + (size_t)r * NC * colstride;
+      cpx<T>* Zr = a.Z + (size_t)r * NC * colstride;
+      cpx<T> bp[NC], bn[NC];
+#pragma unroll
+      for (int l = 0; l < NC; ++l) {
+        bp[l] = Yr[l * colstride + off_p];
+        bn[l] = Yr[l * colstride + off_n];
+      }
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        cpx<T> ap{T(0), T(0)}, an{T(0), T(0)};
+#pragma unroll
+        for (int l = 0; l < NC; ++l) {
+          const int lo = k < l ? k : l, hi = k < l ? l : k;
+          const T w = av[lo * NC - lo * (lo - 1) / 2 + (hi - lo)];
+          ap.x += w * bp[l].x;
+          ap.y += w * bp[l].y;
+          an.x += w * bn[l].x;
+          an.y += w * bn[l].y;
+        }
+        Zr[k * colstride + off_p] = ap;
+        if (n1 != 0) Zr[k * colstride + off_n] = an;
+      }
+    }
+    return;
+  }
   for (int r = 0; r < a.R; ++r) {
     const cpx<T>* Yr = a.Y + (size_t)r * C * colstride;
     cpx<T>* Zr = a.Z + (size_t)r * C * colstride;
