@@ -34,7 +34,9 @@ struct DiagArgs {
   int R;
 };
 
-template <typename T, int D, int CMAX>
+// EXACT: C == CMAX (<= 12); the C(C+1)/2 entries of A' at the frequency are loaded into
+// registers at once, before the right-hand sides.
+template <typename T, int D, int CMAX, bool EXACT>
 __global__ void __launch_bounds__(128) k_diag(DiagArgs<T> a) {
   using C2 = typename Cplx<T>::type;
   const long long il = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -70,6 +72,31 @@ __global__ void __launch_bounds__(128) k_diag(DiagArgs<T> a) {
     return;
   }
   const long long f = lead * (a.M + 1) + il;
+  if constexpr (EXACT) {
+    constexpr int NP = CMAX * (CMAX + 1) / 2;
+    T av[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) av[p] = __ldg(a.A + (size_t)p * a.n_freq + f);
+    for (int r = 0; r < a.R; ++r) {
+      C2* base = a.spec + (size_t)r * CMAX * a.S + s;
+      C2 b[CMAX];
+#pragma unroll
+      for (int k = 0; k < CMAX; ++k) b[k] = base[(size_t)k * a.S];
+#pragma unroll
+      for (int k1 = 0; k1 < CMAX; ++k1) {
+        T re = T(0), im = T(0);
+#pragma unroll
+        for (int k2 = 0; k2 < CMAX; ++k2) {
+          const int lo = k1 < k2 ? k1 : k2, hi = k1 < k2 ? k2 : k1;
+          const T av_ = av[lo * CMAX - lo * (lo - 1) / 2 + (hi - lo)];
+          re += av_ * b[k2].x;
+          im += av_ * b[k2].y;
+        }
+        base[(size_t)k1 * a.S] = C2{re, im};
+      }
+    }
+    return;
+  }
   for (int r = 0; r < a.R; ++r) {
     C2* base = a.spec + (size_t)r * C * a.S + s;
     C2 b[CMAX];
@@ -94,13 +121,23 @@ __global__ void __launch_bounds__(128) k_diag(DiagArgs<T> a) {
   }
 }
 
+template <typename T, int D, int NC>
+void launch_exact(const DiagArgs<T>& a, dim3 grid, cudaStream_t st) {
+  if constexpr (NC <= 12) {
+    if (a.C == NC) {
+      k_diag<T, D, NC, true><<<grid, 128, 0, st>>>(a);
+      return;
+    }
+    launch_exact<T, D, NC + 1>(a, grid, st);
+  }
+}
+
 template <typename T, int D>
 void launch_c(const DiagArgs<T>& a, dim3 grid, cudaStream_t st) {
+  if (a.C <= 12) return launch_exact<T, D, 1>(a, grid, st);
   switch (cmax_bucket(a.C)) {
-    case 8: k_diag<T, D, 8><<<grid, 128, 0, st>>>(a); break;
-    case 12: k_diag<T, D, 12><<<grid, 128, 0, st>>>(a); break;
-    case 16: k_diag<T, D, 16><<<grid, 128, 0, st>>>(a); break;
-    default: k_diag<T, D, 32><<<grid, 128, 0, st>>>(a);
+    case 16: k_diag<T, D, 16, false><<<grid, 128, 0, st>>>(a); break;
+    default: k_diag<T, D, 32, false><<<grid, 128, 0, st>>>(a);
   }
 }
 
