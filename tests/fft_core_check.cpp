@@ -5,7 +5,7 @@
 //
 // stdin:  mode L count, then the input numbers (mode c2c/ic2c: 2*2^L reals as
 //         interleaved complex; r2c: 2^(L+1) reals; c2r: 2*(2^L + 1) reals, the half
-//         spectrum X[0..N2]).
+//         spectrum X[0..N2]).  fc2c/fic2c: c2c/ic2c in float (the FP32 plans' arithmetic).
 // stdout: the output numbers, one per line (c2c/ic2c: 2*2^L; r2c: 2*(2^L + 1);
 //         c2r: 2^(L+1) reals).
 #include <cmath>
@@ -20,25 +20,26 @@ using gpn::fft::Pass;
 using C = cpx<double>;
 
 // a pass with the two-level twiddle (the real split's functor), for the radix-2/4/8 pass
-template <int R, int NB, bool INV>
-void pass2(std::vector<C>& buf, int N, int Ns) {
+template <int R, int NB, bool INV, typename T = double>
+void pass2(std::vector<cpx<T>>& buf, int N, int Ns) {
   const int nt = N / 16;
-  std::vector<Pass<R, NB, double>> st(nt);
+  std::vector<Pass<R, NB, T>> st(nt);
   for (int t = 0; t < nt; ++t) st[t].load(buf.data(), N, t, nt);
-  std::vector<C> hi(N / 64 + 1), lo(64);
-  for (int q = 0; q < (int)hi.size(); ++q) hi[q] = {std::cos(2 * M_PI * (64.0 * q) / N), -std::sin(2 * M_PI * (64.0 * q) / N)};
-  for (int j = 0; j < 64; ++j) lo[j] = {std::cos(2 * M_PI * j / N), -std::sin(2 * M_PI * j / N)};
-  const gpn::fft::Twiddle2<double> t2{hi.data(), lo.data()};
+  std::vector<cpx<T>> hi(N / 64 + 1), lo(64);
+  for (int q = 0; q < (int)hi.size(); ++q)
+    hi[q] = {(T)std::cos(2 * M_PI * (64.0 * q) / N), (T)-std::sin(2 * M_PI * (64.0 * q) / N)};
+  for (int j = 0; j < 64; ++j) lo[j] = {(T)std::cos(2 * M_PI * j / N), (T)-std::sin(2 * M_PI * j / N)};
+  const gpn::fft::Twiddle2<T> t2{hi.data(), lo.data()};
   for (int t = 0; t < nt; ++t) st[t].template store<INV>(buf.data(), t2, N, Ns, t, nt);
 }
 
 // a radix-16 pass with its table from gpn::fft::pass_tables, as on the device
-template <bool INV>
-void pass16(std::vector<C>& buf, const std::vector<C>& tab, int L, int Ns) {
+template <bool INV, typename T = double>
+void pass16(std::vector<cpx<T>>& buf, const std::vector<cpx<T>>& tab, int L, int Ns) {
   const int N = 1 << L, nt = N / 16;
-  std::vector<Pass<16, 1, double>> st(nt);
+  std::vector<Pass<16, 1, T>> st(nt);
   for (int t = 0; t < nt; ++t) st[t].load(buf.data(), N, t, nt);
-  const gpn::fft::PassTwiddle<double> tw{tab.data() + gpn::fft::pass_table_offset(L, Ns), Ns};
+  const gpn::fft::PassTwiddle<T> tw{tab.data() + gpn::fft::pass_table_offset(L, Ns), Ns};
   for (int t = 0; t < nt; ++t) st[t].template store<INV>(buf.data(), tw, N, Ns, t, nt);
 }
 
@@ -79,21 +80,21 @@ void fft_regs(std::vector<C>& buf, int L) {
   }
 }
 
-template <bool INV>
-void fft(std::vector<C>& buf, int L) {
+template <bool INV, typename T = double>
+void fft(std::vector<cpx<T>>& buf, int L) {
   const int N = 1 << L;
   const std::vector<double> raw = gpn::fft::pass_tables(L);
-  std::vector<C> tab(raw.size() / 2 + 1);
-  for (size_t i = 0; i < raw.size() / 2; ++i) tab[i] = {raw[2 * i], raw[2 * i + 1]};
+  std::vector<cpx<T>> tab(raw.size() / 2 + 1);
+  for (size_t i = 0; i < raw.size() / 2; ++i) tab[i] = {(T)raw[2 * i], (T)raw[2 * i + 1]};
   int Ns = 1;
   switch (L % 4) {
-    case 1: pass2<2, 8, INV>(buf, N, Ns); Ns *= 2; break;
-    case 2: pass2<4, 4, INV>(buf, N, Ns); Ns *= 4; break;
-    case 3: pass2<8, 2, INV>(buf, N, Ns); Ns *= 8; break;
+    case 1: pass2<2, 8, INV, T>(buf, N, Ns); Ns *= 2; break;
+    case 2: pass2<4, 4, INV, T>(buf, N, Ns); Ns *= 4; break;
+    case 3: pass2<8, 2, INV, T>(buf, N, Ns); Ns *= 8; break;
     default: break;
   }
   for (int q = 0; q < L / 4; ++q) {
-    pass16<INV>(buf, tab, L, Ns);
+    pass16<INV, T>(buf, tab, L, Ns);
     Ns *= 16;
   }
 }
@@ -107,6 +108,20 @@ int main() {
   auto at = [&](int i) -> C& { return buf[gpn::fft::pad(i)]; };
   std::vector<C> wnf(N + 1);
   for (int k = 0; k <= N; ++k) wnf[k] = {std::cos(M_PI * k / N), -std::sin(M_PI * k / N)};  // W_{2N}^k
+  if (!std::strcmp(mode, "fc2c") || !std::strcmp(mode, "fic2c")) {
+    std::vector<cpx<float>> fb(gpn::fft::pad(N) + 1, cpx<float>{0, 0});
+    for (int i = 0; i < N; ++i) {
+      double re, im;
+      if (std::scanf("%lf %lf", &re, &im) != 2) return 1;
+      fb[gpn::fft::pad(i)] = {(float)re, (float)im};
+    }
+    if (mode[1] == 'i')
+      fft<true, float>(fb, L);
+    else
+      fft<false, float>(fb, L);
+    for (int i = 0; i < N; ++i) std::printf("%.9g\n%.9g\n", fb[gpn::fft::pad(i)].x, fb[gpn::fft::pad(i)].y);
+    return 0;
+  }
   if (!std::strcmp(mode, "c2cr")) {
     for (int i = 0; i < N; ++i) {
       double re, im;

@@ -58,6 +58,21 @@ def test_first_pass_from_registers(driver, L):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("L", [5, 8, 11, 12])
+def test_float_passes(driver, L):
+    """The passes in float (the FP32 plans' arithmetic) stay within a few float roundings
+    of numpy's transform."""
+    n = 1 << L
+    rng = np.random.default_rng(300 + L)
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    inter = np.column_stack([z.real, z.imag]).ravel()
+    for mode, ref in (("fc2c", np.fft.fft(z)), ("fic2c", np.fft.ifft(z) * n)):
+        f = run(driver, mode, L, inter)
+        got = f[0::2] + 1j * f[1::2]
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 2e-6 * L, (mode, err)
+
+
 @pytest.mark.parametrize("L", [4, 7, 10])
 def test_real_split_matches_rfft_and_irfft(driver, L):
     n2 = 1 << L
