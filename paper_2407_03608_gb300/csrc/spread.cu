@@ -361,6 +361,34 @@ void spread_impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st)
 
 }  // namespace
 
+// d = 1 in FP64 with fewer active tiles than SMs (short point sets): the tiled kernel
+// would run a handful of CTAs, and float64 shared-memory atomics are emulated on sm_103.
+// Instead one thread per point evaluates its W kernel values once and adds every
+// (cell, channel) contribution with a native float64 atomic in L2 to the zeroed grid.
+// The summation order varies from run to run at the level of float64 rounding.
+__global__ void __launch_bounds__(128) k_spread1d_atomic(const int* __restrict__ cell0,
+                                                         const double* __restrict__ xi,
+                                                         const double* __restrict__ wk,
+                                                         const double* __restrict__ alpha, long long n, double* grid,
+                                                         long long G, int W, double beta, double inv_halfw, int C) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (p >= n) return;
+  double psi[kMaxWidth];
+  const double x = xi[p];
+#pragma unroll
+  for (int c = 0; c < kMaxWidth; ++c) psi[c] = c < W ? es_psi<double>((double)c - x, beta, inv_halfw) : 0.0;
+  const double amp = alpha[(size_t)r * n + p];
+  double* g = grid + (size_t)r * C * G + cell0[p];
+  for (int k = 0; k < C; ++k) {
+    const double v = wk[(size_t)p * C + k] * amp;
+    double* gk = g + (size_t)k * G;
+#pragma unroll
+    for (int c = 0; c < kMaxWidth; ++c)
+      if (c < W) atomicAdd(gk + c, psi[c] * v);
+  }
+}
+
 int spread_pitch(int d, int tile) { return d == 1 ? tile : tile + 1; }
 
 size_t spread_smem_bytes(int d, int tile, int C, size_t rs, int width) {
@@ -373,6 +401,18 @@ size_t spread_smem_bytes(int d, int tile, int C, size_t rs, int width) {
 
 void launch_spread(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
   if (plan.sp2_tiles) return launch_spread2d(plan, alpha_sorted, R, st);
+  const GridGeom& g = plan.geom;
+  if (g.d == 1 && plan.precision == GP_FP64 && plan.n_active_tiles < 152) {
+    const PointSet& ps = plan.pts;
+    GPN_CUDA(cudaMemsetAsync(plan.grid, 0, sizeof(double) * (size_t)g.C * R * plan.grid_elems, st));
+    if (ps.n == 0) return;
+    dim3 grid((unsigned)((ps.n + 127) / 128), (unsigned)R);
+    k_spread1d_atomic<<<grid, 128, 0, st>>>(ps.cell0[0], (const double*)ps.xi[0], (const double*)ps.wk, alpha_sorted,
+                                            ps.n, (double*)plan.grid, plan.grid_elems, g.width, g.beta,
+                                            2.0 / g.width, g.C);
+    GPN_CUDA(cudaGetLastError());
+    return;
+  }
   if (plan.precision == GP_FP32)
     spread_impl<float>(plan, alpha_sorted, R, st);
   else
