@@ -30,6 +30,7 @@ struct DiagArgs {
   long long M;
   long long n_freq;
   long long row0;                 // first spectrum row of this launch
+  int d;
   int C;
   int R;
 };
@@ -121,6 +122,58 @@ __global__ void __launch_bounds__(128) k_diag(DiagArgs<T> a) {
   }
 }
 
+// Short spectra with more than 12 channels (1-D plans): one thread per (frequency,
+// output channel), blockDim = (32 frequencies, C channels).  The block stages the C
+// inputs of its frequencies in shared memory before any output is written (step 3 runs
+// in place), so C times more threads share the work than in k_diag.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_diag_small(DiagArgs<T> a) {
+  using C2 = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* s_b = reinterpret_cast<C2*>(smem_raw);   // [C][32]
+  const int tx = threadIdx.x, k1 = threadIdx.y, C = a.C;
+  const long long il = blockIdx.x * 32ll + tx;
+  const long long row = a.row0 + blockIdx.y;
+  bool inbox = il <= a.M;
+  long long lead = 0;
+  {
+    long long rest = row;
+    long long mq[kMaxDim];
+    for (int q = a.d - 2; q >= 0; --q) {
+      const long long i = rest % a.nf;
+      rest /= a.nf;
+      mq[q] = (i <= a.nf / 2) ? i : i - a.nf;
+    }
+    for (int q = 0; q < a.d - 1; ++q) {
+      inbox = inbox && mq[q] >= -a.M && mq[q] <= a.M;
+      lead = lead * (2 * a.M + 1) + (mq[q] + a.M);
+    }
+  }
+  const bool valid = il < a.half;
+  const long long s = row * a.half + il;
+  const long long f = lead * (a.M + 1) + il;
+  const int rowp = k1 * C - (k1 * (k1 - 1)) / 2;   // packed index of (k1, k1)
+  for (int r = 0; r < a.R; ++r) {
+    C2* base = a.spec + (size_t)r * C * a.S + s;
+    s_b[k1 * 32 + tx] = valid ? base[(size_t)k1 * a.S] : C2{T(0), T(0)};
+    __syncthreads();
+    if (valid) {
+      C2 out{T(0), T(0)};
+      if (inbox) {
+        for (int k2 = 0; k2 < C; ++k2) {
+          const int p = k2 >= k1 ? rowp + (k2 - k1) : k2 * C - (k2 * (k2 - 1)) / 2 + (k1 - k2);
+          const T av = __ldg(a.A + (size_t)p * a.n_freq + f);
+          const C2 b = s_b[k2 * 32 + tx];
+          out.x += av * b.x;
+          out.y += av * b.y;
+        }
+      }
+      base[(size_t)k1 * a.S] = out;
+    }
+    __syncthreads();   // s_b is refilled for the next rhs
+  }
+}
+
 template <typename T, int D, int NC>
 void launch_exact(const DiagArgs<T>& a, dim3 grid, cudaStream_t st) {
   if constexpr (NC <= 12) {
@@ -154,7 +207,19 @@ void diag_impl(Plan& plan, int R, cudaStream_t st) {
   a.n_freq = plan.n_freq;
   a.C = g.C;
   a.R = R;
+  a.d = g.d;
   const long long rows = a.S / a.half;
+  if (g.C > 12 && a.S * g.C <= 152ll * 2048) {
+    // short spectrum, many channels: thread per (frequency, output channel)
+    const size_t smem = sizeof(typename Cplx<T>::type) * 32 * g.C;
+    for (long long r0 = 0; r0 < rows; r0 += 65535) {
+      a.row0 = r0;
+      dim3 grid((unsigned)((a.half + 31) / 32), (unsigned)std::min<long long>(65535, rows - r0));
+      k_diag_small<T><<<grid, dim3(32, g.C), smem, st>>>(a);
+    }
+    GPN_CUDA(cudaGetLastError());
+    return;
+  }
   // gridDim.y is limited to 65535: launch the rows in chunks
   for (long long r0 = 0; r0 < rows; r0 += 65535) {
     a.row0 = r0;

@@ -57,6 +57,7 @@ def small_case(d, n, seed):
 CASES = [
     # d, N, nu, n_t, n_sigma, M
     (1, 700, 1.5, 24, 10, 300),
+    (1, 600, 1.5, 20, 14, 200),     # 15 channels: the short-spectrum step-3 kernel (transform 1)
     (2, 500, 1.5, 16, 6, 36),
     (3, 300, 2.5, 12, 5, 10),
 ]
