@@ -412,9 +412,21 @@ def measure_config1(dev):
     x = torch.empty_like(y)
     its = []
     solve_ms = _events_ms(lambda: its.append(abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-8, 20000)[1][0]), 3)
+    x64 = x.clone()
+    # the same solve with FP32 inner CG inside FP64 refinement (residuals on the FP64 plan)
+    lo = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev), torch.from_numpy(w.l).to(dev),
+                  nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, **plan.matched_opts())
+    xr = torch.empty_like(y)
+    ref_its = []
+    ref_ms = _events_ms(lambda: ref_its.append(
+        abi.gp_cg_solve_refined(lo.handle, plan.handle, y, xr, 1, w.eta ** 2, 1e-8, 1e-4, 10, 20000)[1][0]), 3)
+    ref_err = float((xr - x64).norm() / x64.norm())
+    lo.close()
     plan.close()
     return {"workload": w.name, "precision": "fp64", "matvec_us": round(mv_ms * 1e3, 2),
-            "cg_solve_ms": round(solve_ms, 3), "cg_iters": int(its[-1]), "rtol": 1e-8}
+            "cg_solve_ms": round(solve_ms, 3), "cg_iters": int(its[-1]), "rtol": 1e-8,
+            "refined_solve": {"precision": "fp32 inner CG, fp64 refinement", "ms": round(ref_ms, 3),
+                              "inner_iters": int(ref_its[-1]), "rel_diff_vs_fp64_cg": ref_err}}
 
 
 def measure_batched(dev, n, R=8, steps=3):
