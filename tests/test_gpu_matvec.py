@@ -125,6 +125,33 @@ def test_pruned_transforms_match_full_grid(gpn, precision, transform):
         assert e <= (1e-12 if precision == "fp64" else 2e-6), (seed, e)
 
 
+@pytest.mark.parametrize("nf", [512, 8192])
+def test_row_kernels_at_forced_grid_sizes(gpn, nf):
+    """FP32 transposed transforms at grid sizes the plans from eps do not pick here:
+    nf = 512 against the exact NUDFT, nf = 8192 (the benchmark's row length) against the
+    full-grid cuFFT path on the same parameters."""
+    w = gpinputs.config_2d(500 if nf == 512 else 3000, 1.5)
+    X = w.points
+    if nf == 512:
+        wp, sig = okern.paper_fields(w.s, w.l, 2)
+        p = explicit_params(2, 1.5, sig, X, n_t=16, n_sigma=6, M=36)
+        plan = gpn.Plan(X, w.s, w.l, nu=1.5, eps=1e-6, precision=gpn.GP_FP32, nufft_tol=1e-6, transform=3, nf=nf,
+                        **plan_kwargs(p))
+        assert plan.info["nf"] == nf and plan.info["transform"] == 3
+        alpha = gpinputs.random_alpha(w.N, 1, seed=61)
+        e = rel(plan.matvec(torch.from_numpy(alpha).cuda()).cpu().numpy(), ktilde.matvec(X, wp, sig, alpha, p))
+        assert e <= 1e-4, e
+    else:
+        full = gpn.Plan(X, w.s, w.l, nu=1.5, eps=1e-5, precision=gpn.GP_FP32, transform=1, nf=nf)
+        pruned = gpn.Plan(X, w.s, w.l, nu=1.5, eps=1e-5, precision=gpn.GP_FP32, transform=3, nf=nf,
+                          **full.matched_opts())
+        assert pruned.info["nf"] == nf
+        for seed in (62, 63):
+            a = torch.from_numpy(gpinputs.random_alpha(w.N, 1, seed=seed)).cuda()
+            e = rel(pruned.matvec(a).cpu().numpy(), full.matvec(a).cpu().numpy())
+            assert e <= 2e-6, (seed, e)
+
+
 def test_shift_adds_eta2_alpha(gpn):
     w = gpinputs.config_1d(300)
     plan = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-6)
