@@ -365,6 +365,9 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
     }
   }
   select_hyper(h, o, o.precision, N);
+  GPN_CHECK(d == 1 || (h.nf * (long long)plan->real_size) % 16 == 0, GP_EINVAL,
+            "nf must be a multiple of 4 (FP32) or 2 (FP64) for d >= 2: the interpolation's TMA copies need "
+            "16-byte row strides");
   const int C = h.n_sigma + 1;
   h.tile = (o.set & GP_SET_TILE) ? o.tile : choose_tile(d, C, plan->real_size, h.width);
   GPN_CHECK(d == 1 || (h.tile * plan->real_size) % 16 == 0, GP_EINVAL,

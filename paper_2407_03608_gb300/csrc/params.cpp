@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <limits>
 
 namespace gpn {
@@ -244,9 +245,16 @@ double inv_gamma_q(double a, double target) {
 
 // Fine-grid sizes: powers of two (the pruned row transforms of d <= 2 need them,
 // and cuFFT is fastest there), and also 3 * 2^a in 3-D.
+// Fine-grid sizes: powers of two for d <= 2 (the custom row transforms are radix 2^k);
+// for d = 3 (cuFFT) any 7-smooth multiple of 4 (the interpolation's TMA copies need row
+// strides of whole 16-byte units: nf * 4 bytes in FP32).
 bool fft_friendly(long long n, int d) {
+  if (d == 3 && n % 4 != 0) return false;
   while (n % 2 == 0) n /= 2;
-  return n == 1 || (d == 3 && n == 3);
+  if (d != 3) return n == 1;
+  for (long long p : {3ll, 5ll, 7ll})
+    while (n % p == 0) n /= p;
+  return n == 1;
 }
 
 // Spreading width for a NUFFT tolerance at upsampling sigma: the ES kernel's
@@ -307,7 +315,7 @@ double es_kernel(double s, int width, double beta) {
   return std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
 }
 
-void select_hyper(Hyper& h, const gp_plan_opts& o, int precision, long long /*n_points*/) {
+void select_hyper(Hyper& h, const gp_plan_opts& o, int precision, long long n_points) {
   const double eps = h.eps;
   const int d = h.d;
   // ---- stage 1: t quadrature -------------------------------------------------
@@ -407,6 +415,46 @@ void select_hyper(Hyper& h, const gp_plan_opts& o, int precision, long long /*n_
     if (fits || (o.set & GP_SET_NF)) break;
     ++nf;
     while (!fft_friendly(nf, d)) ++nf;
+  }
+  // d = 3: pick nf by a cost model measured on the GB300 (FP32, 10 channels):
+  //   FFTs:  rate(nf) s per cell and channel for the forward and inverse transform together
+  //          (cuFFT batched 3-D R2C + C2R; the rate depends on the size's factors: 768 and
+  //          840 run at 3.4e-11 and 5.2e-11, 864 and 1024 at 2.1e-11 and 1.8e-11);
+  //   spreading + interpolation: 4.3e-12 s per point, channel and support cell (width^3),
+  //          times 1.5 above width 9 (a bin tile of 8 cells no longer holds the support:
+  //          channel chunks, fewer CTAs an SM).
+  // Candidates are the measured sizes (below 240 any 7-smooth size at 2e-11, above 1024
+  // powers of two at 1.8e-11) from the smallest admissible one up to 2.5 times the modes.
+  // Measured on the 3-D N = 2e6 workload at eps = 1e-6: nf 768 (width 11) -> 864 (width 9)
+  // took a CG iteration from 328 to 192 ms.
+  if (d == 3 && !(o.set & GP_SET_NF)) {
+    static const std::pair<int, double> kRate[] = {{240, 1.95e-11}, {250, 2.10e-11}, {252, 1.97e-11}, {256, 1.21e-11}, {270, 1.95e-11}, {280, 2.22e-11}, {288, 1.90e-11}, {294, 3.35e-11}, {300, 2.06e-11}, {320, 1.99e-11}, {336, 2.19e-11}, {350, 2.41e-11}, {360, 1.90e-11}, {378, 1.78e-11}, {384, 1.92e-11}, {392, 2.07e-11}, {400, 2.86e-11}, {420, 2.13e-11}, {432, 1.91e-11}, {448, 2.47e-11}, {450, 2.32e-11}, {480, 2.19e-11}, {486, 2.94e-11}, {490, 2.01e-11}, {500, 1.97e-11}, {504, 1.89e-11}, {512, 1.43e-11}, {540, 2.04e-11}, {560, 1.97e-11}, {576, 2.16e-11}, {588, 2.09e-11}, {600, 2.59e-11}, {630, 1.98e-11}, {640, 1.96e-11}, {648, 2.46e-11}, {672, 2.51e-11}, {686, 2.74e-11}, {700, 1.92e-11}, {720, 1.92e-11}, {750, 2.16e-11}, {756, 3.99e-11}, {768, 3.44e-11}, {784, 2.45e-11}, {800, 2.06e-11}, {810, 4.28e-11}, {840, 5.22e-11}, {864, 2.09e-11}, {882, 4.09e-11}, {896, 2.55e-11}, {900, 3.84e-11}, {960, 4.36e-11}, {972, 3.33e-11}, {980, 4.48e-11}, {1000, 2.06e-11}, {1008, 3.07e-11}, {1024, 1.80e-11}};
+    auto rate = [&](long long c) -> double {
+      if (!fft_friendly(c, 3)) return 0.0;
+      if (c < 240) return 2.0e-11;
+      if (c > 1024) return (c & (c - 1)) == 0 ? 1.8e-11 : 0.0;
+      for (const auto& e : kRate)
+        if (e.first == c) return e.second;
+      return 0.0;
+    };
+    double best = -1.0;
+    long long best_nf = nf;
+    const double npts = (double)std::max<long long>(n_points, 1);
+    for (long long c = nf; c <= (long long)(2.5 * modes) + 16; ++c) {
+      const double rc = rate(c);
+      if (rc <= 0.0) continue;
+      const int w = width_for(h.nufft_tol, (double)c / modes);
+      if (w > kMaxWidth || L / P * c + w + 4 > c) continue;
+      const double cost = rc * (double)c * c * c + 4.3e-12 * npts * w * w * w * (w > 9 ? 1.5 : 1.0);
+      if (best < 0.0 || cost < best) {
+        best = cost;
+        best_nf = c;
+      }
+    }
+    nf = best_nf;
+    h.nf = nf;
+    h.upsamp = (double)nf / modes;
+    h.width = width_for(h.nufft_tol, h.upsamp);
   }
   GPN_CHECK(h.width <= kMaxWidth, GP_EINVAL, "spreading kernel wider than 16 cells: raise nf or nufft_tol");
   GPN_CHECK(L / P * h.nf + h.width + 4 <= h.nf, GP_EINVAL, "points do not fit in the fine grid without wrap-around");
