@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
     __syncthreads();  // the previous chunk has been read (and the barrier initialised)
     int nl0[kMaxDim];
     T nx[kMaxDim];
-    if constexpr (D <= 2) load_pt(warp * ppw, nl0, nx);   // d = 3: one point a warp, loaded in place
+    load_pt(warp * ppw, nl0, nx);
     if (TMA) {
       if (threadIdx.x == 0) {
         mbar_expect_tx(bar, a.box_bytes);
@@ -176,16 +176,12 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
       const int p = p0 + (active ? pi : 0);
       int l0[kMaxDim];
       T x[kMaxDim];
-      if constexpr (D <= 2) {
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
-          l0[q] = nl0[q];
-          x[q] = nx[q];
-        }
-        if (pb + nwarps * ppw < npts) load_pt(pb + nwarps * ppw, nl0, nx);
-      } else {
-        load_pt(pb, l0, x);
+      for (int q = 0; q < D; ++q) {
+        l0[q] = nl0[q];
+        x[q] = nx[q];
       }
+      if (pb + nwarps * ppw < npts) load_pt(pb + nwarps * ppw, nl0, nx);
       // the epilogue's own inputs, loaded before the accumulation so their latency is hidden
       T wk_gl = T(0);
       double shift_al = 0.0;
