@@ -155,6 +155,18 @@ typedef struct gp_plan_info {
  * of them to tiles and returns how many there are (or a negative gp_status). */
 int gp_tile_candidates(int d, int n_channels, int precision, int width, int* tiles, int max_tiles);
 
+/* The parameters a plan would get, and its device footprint, without building it and
+ * without a GPU (host only).  The data enter through their ranges: sigma_min..sigma_max,
+ * the paper's horizontal scale sigma(x_i) (sigma = l / sqrt(2) for GP_PARAMS_SCALES),
+ * and the box box_lo[q] <= x_iq <= box_hi[q] (d entries each).  The hyperparameters are
+ * chosen as gp_plan chooses them (Sec. 5.4 recipe, fine grid, tile, transform mode,
+ * step-3 form).  info->bytes_resident is the estimate of the large allocations that
+ * gp_plan checks against max_bytes.  The free device memory is not known here, so the
+ * memory-lean step 3 is predicted only from max_bytes or an explicit opts->step3.
+ * Errors: GP_EINVAL, GP_EUNSUPPORTED as for gp_plan. */
+int gp_plan_params(int d, long long N, double nu, double eps, double sigma_min, double sigma_max,
+                   const double* box_lo, const double* box_hi, const gp_plan_opts* opts, gp_plan_info* info);
+
 /* Fill opts with the defaults (all zero except max_rhs = 1). */
 void gp_plan_opts_default(gp_plan_opts* opts);
 

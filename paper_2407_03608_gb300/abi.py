@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "GP_OK", -1: "GP_EINVAL", -2: "GP_ENOMEM", -3: "GP_ECUDA", -4
 #: every symbol include/gpnufft.h declares
 EXPORTED = ["gp_plan_opts_default", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined",
             "gp_posterior_mean", "gp_posterior_mean_noalloc", "gp_posterior_variance", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
-            "gp_version", "gp_tile_candidates"]
+            "gp_version", "gp_tile_candidates", "gp_plan_params"]
 
 
 class gp_plan_opts(ctypes.Structure):
@@ -113,6 +113,11 @@ def _load():
     lib.gp_tile_candidates.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     lib.gp_tile_candidates.restype = ctypes.c_int
+    lib.gp_plan_params.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(gp_plan_opts),
+                                   ctypes.POINTER(gp_plan_info)]
+    lib.gp_plan_params.restype = ctypes.c_int
     return lib
 
 
@@ -275,6 +280,17 @@ def gp_destroy(plan):
 
 def gp_version() -> str:
     return LIB.gp_version().decode()
+
+
+def gp_plan_params(d: int, N: int, nu: float, eps: float, sigma_min: float, sigma_max: float, box_lo, box_hi,
+                   opts: gp_plan_opts = None) -> dict:
+    """The plan gp_plan would build for data with these ranges, and its footprint (no GPU)."""
+    lo = (ctypes.c_double * 3)(*[float(v) for v in box_lo] + [0.0] * (3 - len(box_lo)))
+    hi = (ctypes.c_double * 3)(*[float(v) for v in box_hi] + [0.0] * (3 - len(box_hi)))
+    info = gp_plan_info()
+    check(LIB.gp_plan_params(int(d), int(N), float(nu), float(eps), float(sigma_min), float(sigma_max), lo, hi,
+                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(info)))
+    return info.as_dict()
 
 
 def gp_tile_candidates(d: int, n_channels: int, precision: int, width: int) -> list:

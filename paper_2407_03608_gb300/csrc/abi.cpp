@@ -300,6 +300,110 @@ void make_tensor_map(Plan& plan) {
   GPN_CHECK(r == CUDA_SUCCESS, GP_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
 }
 
+}  // namespace
+
+// The hyperparameters, layout and device footprint of a plan, from the data's ranges
+// (sigma in [smin, smax], points in the box [lo, hi]); host only.  free_b: device memory
+// available to the plan (-1: unknown, then the memory-lean step 3 is chosen only by
+// max_bytes or explicitly).  tb, when given, receives the plan's tables.
+PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_opts& o, double smin, double smax,
+                     const double* lo_in, const double* hi_in, long long free_b, Tables* tb) {
+  PlanShape ps;
+  Hyper& h = ps.h;
+  const int max_rhs = o.max_rhs > 0 ? o.max_rhs : 1;
+  const size_t rs = o.precision == GP_FP32 ? 4 : 8;
+  h.d = d;
+  h.family = o.family;
+  h.nu = o.family == GP_SE ? INFINITY : nu;
+  h.eps = eps;
+  if (o.set & GP_SET_SIGMA_RANGE) {
+    GPN_CHECK(o.sigma_lo > 0.0 && o.sigma_hi >= o.sigma_lo, GP_EINVAL, "need 0 < sigma_lo <= sigma_hi");
+    GPN_CHECK(smin >= o.sigma_lo * (1 - 1e-12) && smax <= o.sigma_hi * (1 + 1e-12), GP_EINVAL,
+              "data sigma outside [sigma_lo, sigma_hi]");
+    h.sig_lo = o.sigma_lo;
+    h.sig_hi = o.sigma_hi;
+  } else if (smax - smin <= 1e-12 * smax) {
+    h.sig_lo = h.sig_hi = smax;
+  } else {
+    double pad = 0.01 * smax;
+    h.sig_lo = std::max(smin - pad, 0.5 * smin);
+    h.sig_hi = smax + pad;
+  }
+  for (int q = 0; q < d; ++q) {
+    double lo = lo_in[q], hi = hi_in[q];
+    if (o.set & GP_SET_BOX) {
+      GPN_CHECK(o.box_hi[q] > o.box_lo[q], GP_EINVAL, "box_hi must exceed box_lo");
+      GPN_CHECK(lo >= o.box_lo[q] && hi <= o.box_hi[q], GP_EINVAL, "points outside the given box");
+      h.box_lo[q] = o.box_lo[q];
+      h.box_hi[q] = o.box_hi[q];
+    } else {
+      double m = 1e-9 * std::max(hi - lo, 1e-3) + 1e-12;
+      h.box_lo[q] = lo - m;
+      h.box_hi[q] = hi + m;
+    }
+  }
+  select_hyper(h, o, o.precision, N);
+  GPN_CHECK(d == 1 || (h.nf * (long long)rs) % 16 == 0, GP_EINVAL,
+            "nf must be a multiple of 4 (FP32) or 2 (FP64) for d >= 2: the interpolation's TMA copies need "
+            "16-byte row strides");
+  const int C = h.n_sigma + 1;
+  ps.C = C;
+  h.tile = (o.set & GP_SET_TILE) ? o.tile : choose_tile(d, C, rs, h.width);
+  GPN_CHECK(d == 1 || (h.tile * rs) % 16 == 0, GP_EINVAL,
+            "tile must be a multiple of 16 bytes of grid values (4 in FP32, 2 in FP64) for d >= 2");
+  GPN_CHECK(h.tile >= h.width - 1 && h.tile >= 1, GP_EINVAL, "tile must be >= kernel width - 1");
+  Tables local;
+  Tables& t = tb ? *tb : local;
+  build_tables(h, t);
+
+  long long G = 1;
+  for (int q = 0; q < d; ++q) G *= h.nf;
+  const long long S = G / h.nf * (h.nf / 2 + 1);
+  long long nfreq = 1;
+  for (int q = 0; q < d - 1; ++q) nfreq *= (2 * h.M + 1);
+  nfreq *= (h.M + 1);
+  GPN_CHECK(o.transform >= 0 && o.transform <= 3, GP_EINVAL, "transform must be 0, 1, 2 or 3");
+  const bool row_ok = rowfft_supported(d, h.nf, rs);
+  const bool t3_ok = tr3_supported(d, h.nf, rs);
+  GPN_CHECK(o.transform != 2 || row_ok, GP_EUNSUPPORTED, "pruned row transforms need d <= 2 and power-of-two nf");
+  GPN_CHECK(o.transform != 3 || t3_ok, GP_EUNSUPPORTED, "transposed pruned transforms need d = 2 and nf = 2^a");
+  // auto: the transposed pruned transforms for d = 2; the pruned row transforms for
+  // d = 1 in FP64 (FP64 FFT arithmetic is ALU-bound on GB300); else full-grid cuFFT
+  ps.tr3 = o.transform == 3 || (o.transform == 0 && t3_ok);
+  ps.rowfft = o.transform == 2 || (o.transform == 0 && !ps.tr3 && row_ok && o.precision == GP_FP64);
+  if (ps.tr3) nfreq = (h.M + 1) * (h.M + 1);
+  ps.G = G;
+  ps.S = S;
+  ps.nfreq = nfreq;
+  ps.a_bytes = (long long)(C * (C + 1) / 2) * nfreq * (long long)rs;
+  ps.lean_bytes = (long long)t.vt.size() * (h.M + 1) * lean_channel_pitch(C, rs) * (long long)rs;
+  // the large allocations: spreading and interpolation grids, spectra or the pruned
+  // transforms' column buffers, per-point data and the nine work vectors
+  const long long CR = (long long)C * max_rhs;
+  const long long spectra = (ps.tr3 || ps.rowfft) ? 3 * (d == 2 ? h.nf : 1) * CR * (h.M + 1) * 2 * (long long)rs
+                                                  : CR * S * 2 * (long long)rs;
+  ps.est_rest = 2 * CR * G * (long long)rs + spectra + N * (long long)(d * (4 + rs) + 8 + C * rs) +
+                (long long)N * max_rhs * 8 * 9;
+  // step 3: the stored tensor A' (1) or the memory-lean form from per-dimension
+  // factors (2); auto takes the tensor unless it alone breaks max_bytes or the free
+  // device memory
+  GPN_CHECK(o.step3 >= 0 && o.step3 <= 2, GP_EINVAL, "step3 must be 0, 1 or 2");
+  GPN_CHECK(o.step3 != 2 || !ps.rowfft, GP_EUNSUPPORTED,
+            "the memory-lean step 3 runs with transform 1 or 3, not the pruned row transforms");
+  if (o.step3 == 2) {
+    ps.lean = true;
+  } else if (o.step3 == 0 && !ps.rowfft) {
+    const long long with_a = ps.est_rest + ps.a_bytes, with_f = ps.est_rest + ps.lean_bytes;
+    const bool over_budget = o.max_bytes > 0 && with_a > o.max_bytes && with_f <= o.max_bytes;
+    const bool over_free = free_b >= 0 && with_a > free_b && with_f <= free_b;
+    ps.lean = over_budget || over_free;
+  }
+  ps.est = ps.est_rest + (ps.lean ? ps.lean_bytes : ps.a_bytes);
+  return ps;
+}
+
+namespace {
+
 Plan* make_plan(const double* points, long long N, int d, const double* fa, const double* fb, double nu, double eps,
                 const gp_plan_opts& o, cudaStream_t st) {
   GPN_CHECK(d >= 1 && d <= 3, GP_EINVAL, "d must be 1, 2 or 3");
@@ -332,49 +436,14 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   GPN_CHECK(stats[8] == 0.0, GP_EINVAL,
             std::to_string((long long)stats[8]) + " invalid entries (non-finite point, scale <= 0 or weight < 0)");
 
+  size_t free_b = 0, total_b = 0;
+  GPN_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const PlanShape ps = plan_shape(d, N, nu, eps, o, stats[0], stats[1], stats + 2, stats + 5, (long long)free_b,
+                                  &plan->tb);
   Hyper& h = plan->h;
-  h.d = d;
-  h.family = o.family;
-  h.nu = o.family == GP_SE ? INFINITY : nu;
-  h.eps = eps;
-  double smin = stats[0], smax = stats[1];
-  if (o.set & GP_SET_SIGMA_RANGE) {
-    GPN_CHECK(o.sigma_lo > 0.0 && o.sigma_hi >= o.sigma_lo, GP_EINVAL, "need 0 < sigma_lo <= sigma_hi");
-    GPN_CHECK(smin >= o.sigma_lo * (1 - 1e-12) && smax <= o.sigma_hi * (1 + 1e-12), GP_EINVAL,
-              "data sigma outside [sigma_lo, sigma_hi]");
-    h.sig_lo = o.sigma_lo;
-    h.sig_hi = o.sigma_hi;
-  } else if (smax - smin <= 1e-12 * smax) {
-    h.sig_lo = h.sig_hi = smax;
-  } else {
-    double pad = 0.01 * smax;
-    h.sig_lo = std::max(smin - pad, 0.5 * smin);
-    h.sig_hi = smax + pad;
-  }
-  for (int q = 0; q < d; ++q) {
-    double lo = stats[2 + q], hi = stats[5 + q];
-    if (o.set & GP_SET_BOX) {
-      GPN_CHECK(o.box_hi[q] > o.box_lo[q], GP_EINVAL, "box_hi must exceed box_lo");
-      GPN_CHECK(lo >= o.box_lo[q] && hi <= o.box_hi[q], GP_EINVAL, "points outside the given box");
-      h.box_lo[q] = o.box_lo[q];
-      h.box_hi[q] = o.box_hi[q];
-    } else {
-      double m = 1e-9 * std::max(hi - lo, 1e-3) + 1e-12;
-      h.box_lo[q] = lo - m;
-      h.box_hi[q] = hi + m;
-    }
-  }
-  select_hyper(h, o, o.precision, N);
-  GPN_CHECK(d == 1 || (h.nf * (long long)plan->real_size) % 16 == 0, GP_EINVAL,
-            "nf must be a multiple of 4 (FP32) or 2 (FP64) for d >= 2: the interpolation's TMA copies need "
-            "16-byte row strides");
-  const int C = h.n_sigma + 1;
-  h.tile = (o.set & GP_SET_TILE) ? o.tile : choose_tile(d, C, plan->real_size, h.width);
-  GPN_CHECK(d == 1 || (h.tile * plan->real_size) % 16 == 0, GP_EINVAL,
-            "tile must be a multiple of 16 bytes of grid values (4 in FP32, 2 in FP64) for d >= 2");
-  GPN_CHECK(h.tile >= h.width - 1 && h.tile >= 1, GP_EINVAL, "tile must be >= kernel width - 1");
-  build_tables(h, plan->tb);
-
+  h = ps.h;
+  const int C = ps.C;
+  const size_t rs = plan->real_size;
   GridGeom& g = plan->geom;
   g.d = d;
   g.nf = h.nf;
@@ -384,61 +453,16 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   g.tile = h.tile;
   g.C = C;
   g.M = h.M;
-
-  // footprint check before the large allocations
-  const size_t rs = plan->real_size;
-  long long G = 1;
-  for (int q = 0; q < d; ++q) G *= h.nf;
-  long long S = G / h.nf * (h.nf / 2 + 1);
-  long long nfreq = 1;
-  for (int q = 0; q < d - 1; ++q) nfreq *= (2 * h.M + 1);
-  nfreq *= (h.M + 1);
-  plan->grid_elems = G;
-  plan->spec_elems = S;
-  plan->n_freq = nfreq;
-  GPN_CHECK(o.transform >= 0 && o.transform <= 3, GP_EINVAL, "transform must be 0, 1, 2 or 3");
-  const bool row_ok = rowfft_supported(d, h.nf, rs);
-  const bool t3_ok = tr3_supported(d, h.nf, rs);
-  GPN_CHECK(o.transform != 2 || row_ok, GP_EUNSUPPORTED, "pruned row transforms need d <= 2 and power-of-two nf");
-  GPN_CHECK(o.transform != 3 || t3_ok, GP_EUNSUPPORTED, "transposed pruned transforms need d = 2 and nf = 2^a");
-  // auto: the transposed pruned transforms for d = 2; the pruned row transforms for
-  // d = 1 in FP64 (FP64 FFT arithmetic is ALU-bound on GB300); else full-grid cuFFT
-  plan->tr3 = o.transform == 3 || (o.transform == 0 && t3_ok);
-  plan->rowfft = o.transform == 2 || (o.transform == 0 && !plan->tr3 && row_ok && o.precision == GP_FP64);
-  if (plan->tr3) {
-    nfreq = (h.M + 1) * (h.M + 1);
-    plan->n_freq = nfreq;
-  }
-  const long long a_bytes = (long long)(C * (C + 1) / 2) * nfreq * (long long)rs;
-  const long long lean_bytes =
-      (long long)plan->tb.vt.size() * (h.M + 1) * lean_channel_pitch(C, rs) * (long long)rs;
-  // the large allocations: spreading and interpolation grids, spectra or the pruned
-  // transforms' column buffers, per-point data and the nine work vectors
-  const long long CR = (long long)C * max_rhs;
-  const long long spectra = (plan->tr3 || plan->rowfft)
-                                ? 3 * (d == 2 ? h.nf : 1) * CR * (h.M + 1) * 2 * (long long)rs
-                                : CR * S * 2 * (long long)rs;
-  const long long est_rest = 2 * CR * G * (long long)rs + spectra + N * (long long)(d * (4 + rs) + 8 + C * rs) +
-                             (long long)N * max_rhs * 8 * 9;
-  // step 3: the stored tensor A' (1) or the memory-lean form from per-dimension
-  // factors (2); auto takes the tensor unless it alone breaks max_bytes or the free
-  // device memory
-  GPN_CHECK(o.step3 >= 0 && o.step3 <= 2, GP_EINVAL, "step3 must be 0, 1 or 2");
-  GPN_CHECK(o.step3 != 2 || !plan->rowfft, GP_EUNSUPPORTED,
-            "the memory-lean step 3 runs with transform 1 or 3, not the pruned row transforms");
-  if (o.step3 == 2) {
-    plan->lean = true;
-  } else if (o.step3 == 0 && !plan->rowfft) {
-    size_t free_b = 0, total_b = 0;
-    GPN_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const long long with_a = est_rest + a_bytes, with_f = est_rest + lean_bytes;
-    const bool over_budget = o.max_bytes > 0 && with_a > o.max_bytes && with_f <= o.max_bytes;
-    const bool over_free = with_a > (long long)free_b && with_f <= (long long)free_b;
-    plan->lean = over_budget || over_free;
-  }
-  const long long est = est_rest + (plan->lean ? lean_bytes : a_bytes);
-  GPN_CHECK(o.max_bytes <= 0 || est <= o.max_bytes, GP_ENOMEM,
-            "plan needs about " + std::to_string(est) + " device bytes, above max_bytes");
+  const long long G = ps.G, S = ps.S;
+  plan->grid_elems = ps.G;
+  plan->spec_elems = ps.S;
+  plan->n_freq = ps.nfreq;
+  plan->tr3 = ps.tr3;
+  plan->rowfft = ps.rowfft;
+  plan->lean = ps.lean;
+  const long long a_bytes = ps.a_bytes;
+  GPN_CHECK(o.max_bytes <= 0 || ps.est <= o.max_bytes, GP_ENOMEM,
+            "plan needs about " + std::to_string(ps.est) + " device bytes, above max_bytes");
 
   std::vector<int> bstart;
   build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
@@ -547,6 +571,40 @@ void check_same_hyper(const Plan& a, const Plan& b) {
 }  // namespace gpn
 
 using namespace gpn;
+
+namespace gpn {
+namespace {
+// the hyperparameter fields of gp_plan_info
+void fill_hyper_info(const Hyper& h, gp_plan_info* info) {
+  info->d = h.d;
+  info->family = h.family;
+  info->nu = h.nu;
+  info->eps = h.eps;
+  info->n_t = h.n_t;
+  info->t_min = h.t_min;
+  info->t_max = h.t_max;
+  info->n_sigma = h.n_sigma;
+  info->sigma_lo = h.sig_lo;
+  info->sigma_hi = h.sig_hi;
+  info->M = h.M;
+  info->dw = h.dw;
+  info->nf = h.nf;
+  info->kernel_width = h.width;
+  info->kernel_beta = h.beta;
+  info->upsampfac = h.upsamp;
+  info->nufft_tol = h.nufft_tol;
+  info->tile = h.tile;
+  for (int q = 0; q < 3; ++q) {
+    info->box_lo[q] = h.box_lo[q];
+    info->box_hi[q] = h.box_hi[q];
+  }
+  info->est_err_t = h.est_t;
+  info->est_err_sigma = h.est_sigma;
+  info->est_err_trunc = h.est_trunc;
+  info->est_err_alias = h.est_alias;
+}
+}  // namespace
+}  // namespace gpn
 
 extern "C" {
 
@@ -827,6 +885,38 @@ int gp_profile_read(gp_plan_t plan, double* ms_avg, long long* count) {
     long long n = p->prof.count;
     for (int q = 0; q < 5; ++q) ms_avg[q] = n ? p->prof.acc[q] / n : 0.0;
     if (count) *count = n;
+    return GP_OK;
+  });
+}
+
+int gp_plan_params(int d, long long N, double nu, double eps, double sigma_min, double sigma_max,
+                   const double* box_lo, const double* box_hi, const gp_plan_opts* opts, gp_plan_info* info) {
+  return guarded([&]() {
+    GPN_CHECK(info != nullptr && box_lo != nullptr && box_hi != nullptr, GP_EINVAL, "null info or box");
+    GPN_CHECK(d >= 1 && d <= 3, GP_EINVAL, "d must be 1, 2 or 3");
+    GPN_CHECK(N >= 1, GP_EINVAL, "N must be >= 1");
+    GPN_CHECK(sigma_min > 0.0 && sigma_max >= sigma_min && std::isfinite(sigma_max), GP_EINVAL,
+              "need 0 < sigma_min <= sigma_max");
+    for (int q = 0; q < d; ++q)
+      GPN_CHECK(std::isfinite(box_lo[q]) && std::isfinite(box_hi[q]) && box_hi[q] >= box_lo[q], GP_EINVAL,
+                "bad point box");
+    gp_plan_opts o;
+    gp_plan_opts_default(&o);
+    if (opts) o = *opts;
+    GPN_CHECK(o.family == GP_MATERN || o.family == GP_SE, GP_EINVAL, "family must be GP_MATERN or GP_SE");
+    GPN_CHECK(o.family == GP_SE || (nu > 0.0 && std::isfinite(nu)), GP_EINVAL, "nu must be > 0");
+    GPN_CHECK(eps > 0.0 && eps <= 0.1, GP_EINVAL, "eps must be in (0, 0.1]");
+    GPN_CHECK(o.precision == GP_FP64 || o.precision == GP_FP32, GP_EINVAL, "precision must be GP_FP64 or GP_FP32");
+    const PlanShape ps = plan_shape(d, N, nu, eps, o, sigma_min, sigma_max, box_lo, box_hi, -1, nullptr);
+    std::memset(info, 0, sizeof(*info));
+    fill_hyper_info(ps.h, info);
+    info->N = N;
+    info->precision = o.precision;
+    info->transform = ps.tr3 ? 3 : (ps.rowfft ? 2 : 1);
+    info->bytes_resident = ps.est;
+    info->max_rhs = o.max_rhs > 0 ? o.max_rhs : 1;
+    info->step3 = ps.lean ? 2 : 1;
+    info->diag_correct = o.diag_correct ? 1 : 0;
     return GP_OK;
   });
 }

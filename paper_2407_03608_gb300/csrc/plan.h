@@ -145,6 +145,17 @@ struct Plan {
   cufftHandle inv_plan(int R);
 };
 
+// Hyperparameters, layout and device footprint of a plan (host only; abi.cpp).
+struct PlanShape {
+  Hyper h;
+  int C = 0;
+  bool tr3 = false, rowfft = false, lean = false;
+  long long G = 0, S = 0, nfreq = 0;
+  long long a_bytes = 0, lean_bytes = 0, est_rest = 0, est = 0;
+};
+PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_opts& o, double smin, double smax,
+                     const double* lo, const double* hi, long long free_b, Tables* tb);
+
 // ---- launchers (defined in the .cu files) ---------------------------------------
 
 // Bin and sort points given in caller order (device, row-major N x d), compute xi,

@@ -1,0 +1,112 @@
+"""Plan parameter selection on the host (gp_plan_params), no GPU: the fine-grid rules per
+dimension, the 3-D grid cost model, the transform and step-3 predictions, the footprint
+estimate and argument checks."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def abi():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_03608_gb300 import abi
+    return abi
+
+
+def smooth7(n):
+    for p in (2, 3, 5, 7):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+def params(abi, d, N, eps, smin, smax, nu=1.5, precision=1, **kw):
+    o = abi.default_opts(precision=precision, **kw)
+    return abi.gp_plan_params(d, N, nu, eps, smin, smax, [0.0] * d, [1.0] * d, o)
+
+
+@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("eps", [1e-3, 1e-5])
+def test_grids_up_to_two_dimensions_are_powers_of_two(abi, d, eps):
+    i = params(abi, d, 10_000, eps, 0.01, 0.02)
+    nf, M = i["nf"], i["M"]
+    assert nf & (nf - 1) == 0
+    assert nf >= 1.25 * (2 * M + 1) and nf // 2 < 1.25 * (2 * M + 1) or i["kernel_width"] > 9
+    if d == 2:
+        assert i["transform"] == 3          # the transposed pruned transforms
+    # the points sit inside the grid with the kernel's margin, no wrap-around
+    P = 1.0 / i["dw"]
+    assert 1.0 / P * nf + i["kernel_width"] + 4 <= nf
+
+
+def test_three_dimensional_grid_model(abi):
+    smin, smax = 0.05 / np.sqrt(2), 0.10 / np.sqrt(2)
+    widths = []
+    for N in (2_000, 200_000, 2_000_000):
+        i = params(abi, 3, N, 1e-6, smin, smax, nu=2.5)
+        nf = i["nf"]
+        assert nf % 4 == 0 and smooth7(nf)                      # 16-byte TMA rows, cuFFT-friendly
+        assert nf >= 1.25 * (2 * i["M"] + 1)
+        widths.append(i["kernel_width"])
+    # more points buy a finer grid and a narrower spreading kernel
+    assert widths == sorted(widths, reverse=True)
+    assert widths[-1] <= 9
+    big = params(abi, 3, 2_000_000, 1e-6, smin, smax, nu=2.5)
+    assert (big["nf"], big["kernel_width"], big["tile"]) == (864, 9, 8)
+
+
+def test_three_dimensional_nf_override_and_stride_rule(abi):
+    smin, smax = 0.05 / np.sqrt(2), 0.10 / np.sqrt(2)
+    base = params(abi, 3, 10_000, 1e-4, smin, smax, nu=2.5)
+    o = abi.default_opts(precision=abi.GP_FP32, nf=base["nf"] + 4, set=abi.GP_SET_NF)
+    i = abi.gp_plan_params(3, 10_000, 2.5, 1e-4, smin, smax, [0, 0, 0], [1, 1, 1], o)
+    assert i["nf"] == base["nf"] + 4
+    o = abi.default_opts(precision=abi.GP_FP32, nf=base["nf"] + 2, set=abi.GP_SET_NF)
+    with pytest.raises(abi.GPError) as e:
+        abi.gp_plan_params(3, 10_000, 2.5, 1e-4, smin, smax, [0, 0, 0], [1, 1, 1], o)
+    assert e.value.status == abi.GP_EINVAL and "16-byte" in str(e.value)
+
+
+def test_accuracy_drives_the_mode_count_and_channels(abi):
+    Ms = [params(abi, 2, 50_000, eps, 0.01, 0.02)["M"] for eps in (1e-3, 1e-4, 1e-5, 1e-6)]
+    assert Ms == sorted(Ms) and Ms[0] < Ms[-1]
+    # a wider scale range needs more Chebyshev channels (Lemma interp)
+    narrow = params(abi, 2, 50_000, 1e-6, 0.01, 0.012)["n_sigma"]
+    wide = params(abi, 2, 50_000, 1e-6, 0.01, 0.04)["n_sigma"]
+    assert narrow < wide
+    # constant scale: one channel (the stationary special case)
+    assert params(abi, 2, 50_000, 1e-6, 0.015, 0.015)["n_sigma"] == 0
+    # the squared exponential needs no quadrature in t
+    assert params(abi, 1, 2000, 1e-6, 0.01, 0.02, family=abi.GP_SE)["n_t"] == 0
+
+
+def test_transform_and_step3_predictions(abi):
+    # 1-D in FP64: the pruned row transforms; in FP32: the full-grid cuFFT path
+    assert params(abi, 1, 2000, 1e-6, 0.01, 0.04, precision=abi.GP_FP64)["transform"] == 2
+    assert params(abi, 1, 2000, 1e-6, 0.01, 0.04, precision=abi.GP_FP32)["transform"] == 1
+    smin, smax = 0.05 / np.sqrt(2), 0.10 / np.sqrt(2)
+    full = params(abi, 3, 2_000_000, 1e-6, smin, smax, nu=2.5)
+    assert full["step3"] == 1
+    lean = params(abi, 3, 2_000_000, 1e-6, smin, smax, nu=2.5, step3=2)
+    assert lean["step3"] == 2 and lean["bytes_resident"] < full["bytes_resident"]
+    # auto: the tensor when it fits max_bytes, the lean form when only that fits
+    mid = (lean["bytes_resident"] + full["bytes_resident"]) // 2
+    assert params(abi, 3, 2_000_000, 1e-6, smin, smax, nu=2.5, max_bytes=mid)["step3"] == 2
+    assert params(abi, 3, 2_000_000, 1e-6, smin, smax, nu=2.5, max_bytes=full["bytes_resident"])["step3"] == 1
+
+
+def test_footprint_estimate_scales_with_right_hand_sides(abi):
+    one = params(abi, 2, 100_000, 1e-5, 0.01, 0.02)["bytes_resident"]
+    eight = params(abi, 2, 100_000, 1e-5, 0.01, 0.02, max_rhs=8)["bytes_resident"]
+    assert 5 * one < eight < 8 * one        # grids and spectra per rhs, A' shared
+
+
+def test_invalid_arguments(abi):
+    o = abi.default_opts()
+    for args in [(0, 10, 1.5, 1e-6, 0.01, 0.02), (2, 0, 1.5, 1e-6, 0.01, 0.02), (2, 10, -1.0, 1e-6, 0.01, 0.02),
+                 (2, 10, 1.5, 0.5, 0.01, 0.02), (2, 10, 1.5, 1e-6, 0.02, 0.01), (2, 10, 1.5, 1e-6, 0.0, 0.02)]:
+        with pytest.raises(abi.GPError) as e:
+            abi.gp_plan_params(*args, [0, 0, 0], [1, 1, 1], o)
+        assert e.value.status == abi.GP_EINVAL
+    abi.gp_plan_params(2, 10, 1.5, 1e-3, 0.01, 0.02, [0, 0], [1, 1], o)   # clears the error message
+    assert abi.LIB.gp_last_error() == b""
