@@ -54,6 +54,26 @@ def _rhs(req) -> int:
     return 1 if y.ndim == 1 else int(y.shape[1])
 
 
+def predicted_eps(abi, req, budget: int, eps_target: float) -> Optional[float]:
+    """The finest eps of the ladder (from eps_target) at which the request's FP64 and FP32
+    plans together are predicted to fit `budget` bytes (gp_plan_params: host only, no
+    allocation).  None when even the coarsest level does not fit."""
+    x = np.asarray(req.points, dtype=np.float64)
+    N, d = x.shape
+    sig = np.asarray(req.l, dtype=np.float64) / np.sqrt(2.0)     # GP_PARAMS_SCALES: sigma = l / sqrt(2)
+    lo, hi = x.min(axis=0), x.max(axis=0)
+    r = _rhs(req)
+    for eps in [e for e in EPS_LADDER if e >= eps_target * (1 - 1e-12)]:
+        total = 0
+        for prec in (abi.GP_FP64, abi.GP_FP32):
+            info = abi.gp_plan_params(d, N, req.nu, eps, float(sig.min()), float(sig.max()), lo, hi,
+                                      abi.default_opts(precision=prec, max_rhs=r))
+            total += info["bytes_resident"]
+        if total <= budget:
+            return eps
+    return None
+
+
 def _plan_fitting(gpn, req, budget: int, eps_target: float, precision, extra: Optional[dict] = None):
     """The plan at the finest eps of the ladder (from eps_target) whose footprint fits."""
     last = None
@@ -88,7 +108,10 @@ class Server:
         gpn = self.gpn
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        hi, eps = _plan_fitting(gpn, req, self.budget // 2, self.eps_target, gpn.GP_FP64)
+        # admission by the host-side footprint prediction; building at that level can still
+        # run out of memory, so the ladder continues from there
+        start = predicted_eps(gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
+        hi, eps = _plan_fitting(gpn, req, self.budget // 2, max(start, self.eps_target), gpn.GP_FP64)
         lo = None
         try:
             lo = gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=gpn.GP_FP32,

@@ -1,7 +1,10 @@
-"""Host logic of the request loop (no GPU): the replayed FIFO clock."""
+"""Host logic of the request loop (no GPU): the replayed FIFO clock and the admission
+by predicted footprint."""
 import numpy as np
+import pytest
 
-from paper_2407_03608_gb300.serving import replay_latency
+import gpinputs
+from paper_2407_03608_gb300.serving import EPS_LADDER, predicted_eps, replay_latency
 
 
 def test_idle_server_latency_is_service_time():
@@ -31,3 +34,34 @@ def test_higher_load_never_lowers_latency():
     l2, _ = replay_latency(arr, svc, 0.9)
     assert np.percentile(l2, 99) >= np.percentile(l1, 99) - 1e-12
     assert np.all(l1 >= svc - 1e-12)
+
+
+@pytest.fixture(scope="module")
+def abi():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_03608_gb300 import abi
+    return abi
+
+
+def test_admission_takes_the_finest_eps_that_fits(abi):
+    # d <= 2 and N <= 5e4, as in the bench's served sample (the stream's 3-D requests have
+    # length scales so short that even eps = 1e-4 needs terabytes)
+    reqs = gpinputs.serving_stream(6, n_min=1000, n_max=50_000, dims=(1, 2), nus=(1.5,), max_rhs=2)
+    for req in reqs:
+        roomy = predicted_eps(abi, req, 10 ** 13, 1e-6)
+        assert roomy == 1e-6
+        # the predicted level coarsens as the budget shrinks, and never gets finer
+        levels = [predicted_eps(abi, req, b, 1e-6) for b in (10 ** 13, 10 ** 10, 10 ** 9, 10 ** 8, 10 ** 7)]
+        seen = [EPS_LADDER.index(e) if e is not None else len(EPS_LADDER) for e in levels]
+        assert seen == sorted(seen)
+        assert predicted_eps(abi, req, 1, 1e-6) is None
+        # a coarser target is never refined
+        assert predicted_eps(abi, req, 10 ** 13, 1e-4) == 1e-4
+
+
+def test_short_length_scales_are_admitted_coarser(abi):
+    # a 3-D request of the stream under the 120 GB budget: only a coarse level fits
+    req = gpinputs.serving_stream(8, n_min=1000, n_max=50_000, dims=(3,), nus=(1.5,), max_rhs=1)[0]
+    eps = predicted_eps(abi, req, 120 * 10 ** 9, 1e-6)
+    assert eps is not None and eps >= 1e-4
