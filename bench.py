@@ -53,6 +53,21 @@ def parse():
     return ap.parse_args()
 
 
+def job_totals(ms_total: float, points_per_step: float, ws: int, device=None):
+    """Whole-job figures over the ranks: the slowest rank's elapsed milliseconds and the
+    points all ranks processed per step (replicas may hold different N).  One rank: the
+    arguments unchanged."""
+    if ws <= 1:
+        return float(ms_total), float(points_per_step)
+    import torch
+    import torch.distributed as dist
+    t_ms = torch.tensor([float(ms_total)], dtype=torch.float64, device=device)
+    t_pts = torch.tensor([float(points_per_step)], dtype=torch.float64, device=device)
+    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_pts, op=dist.ReduceOp.SUM)
+    return float(t_ms.item()), float(t_pts.item())
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -231,12 +246,9 @@ def run_ours(args, ws, rank, local):
     cg_steps(plan, min(args.steps, 10), y, x)
     phase_ms, n_rec = abi.gp_profile_read(plan.handle)
     abi.gp_profile_enable(plan.handle, False)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, points_job = job_totals(ms_total, N, ws, dev)
     ms_step = ms_total / iters
-    value = ws * N / (ms_step * 1e-3) / 1e6
+    value = points_job / (ms_step * 1e-3) / 1e6
 
     # end to end through the public API with pinned host buffers: every step copies
     # y in and alpha out (gp_cg_solve with host pointers runs one iteration per call)

@@ -1,0 +1,45 @@
+"""The bench's cross-rank figures (job_totals) with two gloo ranks on the CPU: the job's
+time is the slowest rank's, its throughput counts every rank's points."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    ms, pts = bench.job_totals([5.0, 7.5][rank], [1000, 2500][rank], ws, device="cpu")
+    with open(os.path.join(out_dir, "r%d" % rank), "w") as f:
+        f.write("%r %r" % (ms, pts))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time_and_all_points(tmp_path):
+    ws = 2
+    mp.start_processes(_rank, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, start_method="spawn")
+    for r in range(ws):
+        ms, pts = (float(v) for v in open(tmp_path / ("r%d" % r)).read().split())
+        assert ms == 7.5 and pts == 3500.0
+
+
+def test_one_rank_is_unchanged():
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    assert bench.job_totals(4.0, 123, 1) == (4.0, 123.0)
