@@ -179,7 +179,13 @@ void gp_plan_opts_default(gp_plan_opts* opts);
  *         in (0, 0.1].  It drives every hyperparameter that opts does not set.
  * Builds the quadrature in t (Sec. 3.2), the Chebyshev nodes (Sec. 3.3), the Fourier
  * grid (Sec. 3.4), sorts the points into fine-grid tiles, and precomputes the
- * per-point weights w_k(x_i) (Eq. Wk) and the tensor A[n] (Remark rem:step3).
+ * per-point weights w_k(x_i) (Eq. Wk) and either the tensor A[n] (Remark rem:step3) or,
+ * with opts->step3 (see there), the per-dimension factors of the memory-lean step 3.
+ * The fine grid: a power of two for d <= 2; for d = 3 the 7-smooth multiple of 4 that
+ * minimises a measured FFT + spreading cost for this N (gp_plan_params shows the
+ * choice without a GPU).  opts->autotune times alternative tiles; opts->diag_correct
+ * adds the exact diagonal defect.  Device memory: about info.bytes_resident, checked
+ * against opts->max_bytes before the large allocations.
  * Errors: GP_EINVAL (d not 1..3, N < 1, nu <= 0, eps out of range, non-positive
  * scale, inconsistent overrides), GP_ENOMEM, GP_ECUDA, GP_ECUFFT. On error *out is NULL. */
 int gp_plan(gp_plan_t* out, const double* points, long long N, int d, const double* field_a,
