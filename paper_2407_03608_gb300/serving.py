@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import threading
 import time
 from dataclasses import dataclass
 from typing import List, Optional
@@ -54,22 +55,27 @@ def _rhs(req) -> int:
     return 1 if y.ndim == 1 else int(y.shape[1])
 
 
-def predicted_eps(abi, req, budget: int, eps_target: float) -> Optional[float]:
-    """The finest eps of the ladder (from eps_target) at which the request's FP64 and FP32
-    plans together are predicted to fit `budget` bytes (gp_plan_params: host only, no
-    allocation).  None when even the coarsest level does not fit."""
+def predicted_footprint(abi, req, eps: float) -> int:
+    """Device bytes of the request's FP64 and FP32 plans at `eps`, predicted on the host
+    (gp_plan_params, no allocation)."""
     x = np.asarray(req.points, dtype=np.float64)
     N, d = x.shape
     sig = np.asarray(req.l, dtype=np.float64) / np.sqrt(2.0)     # GP_PARAMS_SCALES: sigma = l / sqrt(2)
     lo, hi = x.min(axis=0), x.max(axis=0)
-    r = _rhs(req)
+    total = 0
+    for prec in (abi.GP_FP64, abi.GP_FP32):
+        info = abi.gp_plan_params(d, N, req.nu, eps, float(sig.min()), float(sig.max()), lo, hi,
+                                  abi.default_opts(precision=prec, max_rhs=_rhs(req)))
+        total += int(info["bytes_resident"])
+    return total
+
+
+def predicted_eps(abi, req, budget: int, eps_target: float) -> Optional[float]:
+    """The finest eps of the ladder (from eps_target) at which the request's FP64 and FP32
+    plans together are predicted to fit `budget` bytes.  None when even the coarsest level
+    does not fit."""
     for eps in [e for e in EPS_LADDER if e >= eps_target * (1 - 1e-12)]:
-        total = 0
-        for prec in (abi.GP_FP64, abi.GP_FP32):
-            info = abi.gp_plan_params(d, N, req.nu, eps, float(sig.min()), float(sig.max()), lo, hi,
-                                      abi.default_opts(precision=prec, max_rhs=r))
-            total += info["bytes_resident"]
-        if total <= budget:
+        if predicted_footprint(abi, req, eps) <= budget:
             return eps
     return None
 
@@ -132,6 +138,127 @@ class Server:
             hi.close()
         return Served(req.rid, req.points.shape[0], req.points.shape[1], req.nu, _rhs(req), eps, t2 - t0, t1 - t0,
                       t2 - t1, iters, relres, nbytes)
+
+    def solve_on(self, req, stream):
+        """One request on `stream`, from the calling host thread, with no device-wide
+        synchronisation (other requests may run on other streams meanwhile): the FP64 and
+        FP32 plans at the admitted eps, then the refined solve.  Returns (alpha, Served)."""
+        gpn = self.gpn
+        sh = stream.cuda_stream
+        t0 = time.perf_counter()
+        start = predicted_eps(gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
+        hi, eps = _plan_fitting(gpn, req, self.budget // 2, max(start, self.eps_target), gpn.GP_FP64,
+                                extra={"stream": sh})
+        lo = None
+        try:
+            lo = gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=gpn.GP_FP32,
+                          max_rhs=_rhs(req), stream=sh, **hi.matched_opts())
+            stream.synchronize()
+            t1 = time.perf_counter()
+            y = np.asarray(req.y, dtype=np.float64)
+            alpha, info = hi.solve_refined(lo, y, req.eta ** 2, rtol=self.rtol, inner_rtol=self.inner_rtol,
+                                           outer_max=self.outer_max, maxit=self.maxit, stream=sh)
+            stream.synchronize()
+            t2 = time.perf_counter()
+            nbytes = int(hi.info["bytes_resident"] + lo.info["bytes_resident"])
+        finally:
+            if lo is not None:
+                lo.close()
+            hi.close()
+        rec = Served(req.rid, req.points.shape[0], req.points.shape[1], req.nu, _rhs(req), eps, t2 - t0, t1 - t0,
+                     t2 - t1, int(np.max(info["iters"])), float(np.max(info["relres"])), nbytes)
+        return np.asarray(alpha), rec
+
+    def serve_concurrent(self, requests, slots: int = 3, arrivals=None):
+        """Continuous batching.  Up to `slots` requests are in flight, each on a CUDA stream
+        of its own driven by a host thread of its own, so their kernels overlap on the
+        device.  A request starts, in arrival order, once it has arrived (`arrivals`:
+        seconds from the start; default all at once), a slot is free, and its predicted
+        footprint fits the HBM budget beside the requests in flight (one request is always
+        admitted).  Returns (results, info): results[i] = (alpha, Served, start_s, end_s) on
+        the wall clock of this call; info holds the makespan and the most requests seen in
+        flight at once."""
+        import torch
+        n = len(requests)
+        arr = np.zeros(n) if arrivals is None else np.asarray(arrivals, dtype=np.float64)
+        order = [int(i) for i in np.argsort(arr, kind="stable")]
+        need = []
+        for req in requests:
+            eps = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
+            need.append(predicted_footprint(self.gpn.abi, req, max(eps, self.eps_target)))
+        cond = threading.Condition()
+        st = {"next": 0, "bytes": 0, "inflight": 0, "max_inflight": 0}
+        results = [None] * n
+        errors = []
+        t_start = time.perf_counter()
+        device = torch.cuda.current_device()
+
+        def worker():
+            torch.cuda.set_device(device)
+            stream = torch.cuda.Stream()
+            while True:
+                with cond:
+                    while True:
+                        if st["next"] >= n or errors:
+                            return
+                        i = order[st["next"]]
+                        wait = arr[i] - (time.perf_counter() - t_start)
+                        fits = st["inflight"] == 0 or st["bytes"] + need[i] <= self.budget
+                        if wait <= 0 and fits:
+                            st["next"] += 1
+                            st["bytes"] += need[i]
+                            st["inflight"] += 1
+                            st["max_inflight"] = max(st["max_inflight"], st["inflight"])
+                            break
+                        cond.wait(timeout=min(max(wait, 1e-3), 0.05) if wait > 0 else 0.05)
+                begin = time.perf_counter() - t_start
+                try:
+                    alpha, rec = self.solve_on(requests[i], stream)
+                    results[i] = (alpha, rec, begin, time.perf_counter() - t_start)
+                except BaseException as e:   # re-raised by the caller after the join
+                    errors.append(e)
+                finally:
+                    with cond:
+                        st["bytes"] -= need[i]
+                        st["inflight"] -= 1
+                        cond.notify_all()
+
+        threads = [threading.Thread(target=worker, daemon=True) for _ in range(max(1, slots))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errors:
+            raise errors[0]
+        return results, {"makespan_s": time.perf_counter() - t_start, "max_inflight": st["max_inflight"]}
+
+    def serve_batched(self, requests, load: float = 0.8, slots: int = 3) -> dict:
+        """Continuous batching measured on the wall clock: capacity from all requests at once
+        (requests per second of makespan), then the stream's Poisson arrivals rescaled to
+        `load` times that capacity, with latency = finish - arrival of each request."""
+        _, first = self.serve_concurrent(requests, slots=slots)
+        capacity = len(requests) / first["makespan_s"]
+        arr = np.array([r.arrival_s for r in requests], dtype=np.float64)
+        span = arr[-1] - arr[0] if len(arr) > 1 else 0.0
+        rate0 = (len(arr) - 1) / span if span > 0 else 1.0
+        rate = load * capacity
+        rel = (arr - arr[0]) * (rate0 / rate)
+        res, info = self.serve_concurrent(requests, slots=slots, arrivals=rel)
+        lat = np.array([r[3] - rel[i] for i, r in enumerate(res)])
+        service = np.array([r[3] - r[2] for r in res])
+        return {
+            "slots": slots,
+            "requests": len(res),
+            "load": load,
+            "offered_rate_per_s": rate,
+            "capacity_solves_per_s": capacity,
+            "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)),
+            "service_p50_s": float(np.percentile(service, 50)),
+            "service_p99_s": float(np.percentile(service, 99)),
+            "max_in_flight": int(info["max_inflight"]),
+            "max_relres": float(max(r[1].relres for r in res)),
+        }
 
     def serve(self, requests, load: float = 0.8) -> dict:
         """Serve all requests; latency statistics at `load` times the measured capacity."""
