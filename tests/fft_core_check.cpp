@@ -1,4 +1,4 @@
-// Host driver for tests/test_fft_core.py: runs the row-FFT building blocks of
+// Host program for tests/test_fft_core.py: runs the row-FFT building blocks of
 // csrc/fft_core.h on the CPU, with the same pass schedule as the device kernels
 // (one pass of radix 2^(L mod 4) first when L is not a multiple of 4, then radix-16
 // passes), emulating the block barrier between the load and store halves of a pass.

@@ -1,7 +1,7 @@
 """The row-FFT building blocks (csrc/fft_core.h) against numpy's FFT, on the CPU.
 
 The shared-memory row transforms of the pruned 2-D FFT are made of in-register DFTs
-(radix 2, 4, 8, 16), Stockham passes and the real/complex split.  The driver
+(radix 2, 4, 8, 16), Stockham passes and the real/complex split.  The host program
 tests/fft_core_check.cpp runs them with the device kernels' pass schedule; here the
 results are compared with numpy.fft (complex forward/inverse, rfft, irfft * n).
 """
@@ -16,50 +16,50 @@ CSRC = os.path.join(ROOT, "paper_2407_03608_gb300", "csrc")
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def host_prog(tmp_path_factory):
     exe = tmp_path_factory.mktemp("fft") / "fft_core_check"
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", CSRC, os.path.join(ROOT, "tests", "fft_core_check.cpp"),
                            "-o", str(exe)])
     return str(exe)
 
 
-def run(driver, mode, L, data):
+def run(host_prog, mode, L, data):
     inp = "%s %d\n" % (mode, L) + "\n".join("%.17g" % v for v in data) + "\n"
-    out = subprocess.run([driver], input=inp, capture_output=True, text=True, check=True).stdout
+    out = subprocess.run([host_prog], input=inp, capture_output=True, text=True, check=True).stdout
     return np.array([float(v) for v in out.split()])
 
 
 @pytest.mark.parametrize("L", [4, 5, 6, 7, 8, 9, 11, 12])
-def test_complex_fft_both_directions(driver, L):
+def test_complex_fft_both_directions(host_prog, L):
     n = 1 << L
     rng = np.random.default_rng(L)
     z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     inter = np.column_stack([z.real, z.imag]).ravel()
-    f = run(driver, "c2c", L, inter)
+    f = run(host_prog, "c2c", L, inter)
     got = f[0::2] + 1j * f[1::2]
     ref = np.fft.fft(z)
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
-    b = run(driver, "ic2c", L, inter)
+    b = run(host_prog, "ic2c", L, inter)
     got = b[0::2] + 1j * b[1::2]
     ref = np.fft.ifft(z) * n                      # unnormalised e^{+2 pi i}
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("L", [4, 5, 6, 7, 8, 12])
-def test_first_pass_from_registers(driver, L):
+def test_first_pass_from_registers(host_prog, L):
     """The row kernels run the first pass on the elements each thread loaded from
     global memory (t + u N/16); the transform is unchanged."""
     n = 1 << L
     rng = np.random.default_rng(200 + L)
     z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-    f = run(driver, "c2cr", L, np.column_stack([z.real, z.imag]).ravel())
+    f = run(host_prog, "c2cr", L, np.column_stack([z.real, z.imag]).ravel())
     got = f[0::2] + 1j * f[1::2]
     ref = np.fft.fft(z)
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("L", [5, 8, 11, 12])
-def test_float_passes(driver, L):
+def test_float_passes(host_prog, L):
     """The passes in float (the FP32 plans' arithmetic) stay within a few float roundings
     of numpy's transform."""
     n = 1 << L
@@ -67,19 +67,19 @@ def test_float_passes(driver, L):
     z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     inter = np.column_stack([z.real, z.imag]).ravel()
     for mode, ref in (("fc2c", np.fft.fft(z)), ("fic2c", np.fft.ifft(z) * n)):
-        f = run(driver, mode, L, inter)
+        f = run(host_prog, mode, L, inter)
         got = f[0::2] + 1j * f[1::2]
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 2e-6 * L, (mode, err)
 
 
 @pytest.mark.parametrize("L", [4, 7, 10])
-def test_real_split_matches_rfft_and_irfft(driver, L):
+def test_real_split_matches_rfft_and_irfft(host_prog, L):
     n2 = 1 << L
     nf = 2 * n2
     rng = np.random.default_rng(100 + L)
     x = rng.standard_normal(nf)
-    f = run(driver, "r2c", L, x)                  # x[2n], x[2n+1] pairs in order
+    f = run(host_prog, "r2c", L, x)                  # x[2n], x[2n+1] pairs in order
     got = f[0::2] + 1j * f[1::2]
     ref = np.fft.rfft(x)
     assert got.shape == ref.shape
@@ -90,6 +90,6 @@ def test_real_split_matches_rfft_and_irfft(driver, L):
     X[:M + 1] = rng.standard_normal(M + 1) + 1j * rng.standard_normal(M + 1)
     X[0] = X[0].real
     inter = np.column_stack([X.real, X.imag]).ravel()
-    y = run(driver, "c2r", L, inter)              # z[n] = x[2n] + i x[2n+1]
+    y = run(host_prog, "c2r", L, inter)              # z[n] = x[2n] + i x[2n+1]
     ref = np.fft.irfft(X, nf) * nf                # unnormalised C2R
     assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
