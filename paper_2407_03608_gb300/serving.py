@@ -14,11 +14,18 @@ GPU and, for each one:
    ``gp_cg_solve_refined`` and copies alpha back to the host;
 4. frees the plans.
 
-Latency is measured per request as finish - arrival on a replayed clock: a request
-starts when it has arrived and the previous one has finished, and its service time is
-the measured wall time of steps 1-4 (host-synchronised).  The arrival times are
-rescaled so that the offered load is a chosen fraction of the measured capacity,
-which gives p50/p99 latency at that load without idling the GPU.
+Two ways of serving share those steps:
+
+* ``Server.serve``: one request at a time.  Latency is finish - arrival on a replayed
+  clock: a request starts when it has arrived and the previous one has finished, and its
+  service time is the measured wall time of steps 1-4 (host-synchronised).  The arrival
+  times are rescaled so that the offered load is a chosen fraction of the measured
+  capacity, which gives p50/p99 latency at that load without idling the GPU.
+* ``Server.serve_concurrent`` / ``serve_batched``: continuous batching.  Up to ``slots``
+  requests are in flight, each on a CUDA stream and host thread of its own, so their
+  kernels overlap on the device; a request is admitted in arrival order as soon as a slot
+  is free and its predicted footprint fits beside the requests in flight.  Latency is
+  measured on the wall clock against arrivals rescaled to the chosen load.
 """
 from __future__ import annotations
 
@@ -96,7 +103,8 @@ def _plan_fitting(gpn, req, budget: int, eps_target: float, precision, extra: Op
 
 
 class Server:
-    """Serves requests one after another on the current CUDA device."""
+    """Serves requests on the current CUDA device, one after another (``serve``) or
+    several in flight on their own streams (``serve_concurrent``, ``serve_batched``)."""
 
     def __init__(self, hbm_budget: float = 120e9, eps_target: float = 1e-6, rtol: float = 1e-8,
                  inner_rtol: float = 1e-4, maxit: int = 20000, outer_max: int = 20):
@@ -179,58 +187,20 @@ class Server:
         the wall clock of this call; info holds the makespan and the most requests seen in
         flight at once."""
         import torch
-        n = len(requests)
-        arr = np.zeros(n) if arrivals is None else np.asarray(arrivals, dtype=np.float64)
-        order = [int(i) for i in np.argsort(arr, kind="stable")]
+        arr = np.zeros(len(requests)) if arrivals is None else np.asarray(arrivals, dtype=np.float64)
         need = []
         for req in requests:
             eps = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
             need.append(predicted_footprint(self.gpn.abi, req, max(eps, self.eps_target)))
-        cond = threading.Condition()
-        st = {"next": 0, "bytes": 0, "inflight": 0, "max_inflight": 0}
-        results = [None] * n
-        errors = []
-        t_start = time.perf_counter()
         device = torch.cuda.current_device()
 
-        def worker():
+        def make_stream():
             torch.cuda.set_device(device)
-            stream = torch.cuda.Stream()
-            while True:
-                with cond:
-                    while True:
-                        if st["next"] >= n or errors:
-                            return
-                        i = order[st["next"]]
-                        wait = arr[i] - (time.perf_counter() - t_start)
-                        fits = st["inflight"] == 0 or st["bytes"] + need[i] <= self.budget
-                        if wait <= 0 and fits:
-                            st["next"] += 1
-                            st["bytes"] += need[i]
-                            st["inflight"] += 1
-                            st["max_inflight"] = max(st["max_inflight"], st["inflight"])
-                            break
-                        cond.wait(timeout=min(max(wait, 1e-3), 0.05) if wait > 0 else 0.05)
-                begin = time.perf_counter() - t_start
-                try:
-                    alpha, rec = self.solve_on(requests[i], stream)
-                    results[i] = (alpha, rec, begin, time.perf_counter() - t_start)
-                except BaseException as e:   # re-raised by the caller after the join
-                    errors.append(e)
-                finally:
-                    with cond:
-                        st["bytes"] -= need[i]
-                        st["inflight"] -= 1
-                        cond.notify_all()
+            return torch.cuda.Stream()
 
-        threads = [threading.Thread(target=worker, daemon=True) for _ in range(max(1, slots))]
-        for t in threads:
-            t.start()
-        for t in threads:
-            t.join()
-        if errors:
-            raise errors[0]
-        return results, {"makespan_s": time.perf_counter() - t_start, "max_inflight": st["max_inflight"]}
+        done, info = run_slots(arr, need, self.budget, slots, lambda i, stream: self.solve_on(requests[i], stream),
+                               make_stream)
+        return [(alpha, rec, begin, end) for (alpha, rec), begin, end in done], info
 
     def serve_batched(self, requests, load: float = 0.8, slots: int = 3) -> dict:
         """Continuous batching measured on the wall clock: capacity from all requests at once
@@ -284,6 +254,64 @@ class Server:
         }
 
 
+def run_slots(arrivals, need, budget: int, slots: int, run, make_ctx=lambda: None):
+    """The scheduler of continuous batching, on the host.  Job i becomes eligible at
+    ``arrivals[i]`` seconds after the start; jobs start in arrival order (ties in index
+    order) on ``slots`` worker threads, each of which calls ``make_ctx()`` once (a CUDA
+    stream, say) and then ``run(i, ctx)`` for the jobs it takes.  Job i holds ``need[i]``
+    bytes of ``budget`` while it runs; the head of the queue waits until it fits beside
+    the jobs in flight, except that a job is always admitted when nothing is in flight.
+    Returns (results, info): results[i] = (run's value, start_s, end_s) on the clock of
+    this call, info = {"makespan_s", "max_inflight"}.  The first exception raised by a
+    job stops further admissions and is re-raised once the running jobs have ended."""
+    n = len(need)
+    arr = np.asarray(arrivals, dtype=np.float64)
+    order = [int(i) for i in np.argsort(arr, kind="stable")]
+    cond = threading.Condition()
+    st = {"next": 0, "bytes": 0, "inflight": 0, "max_inflight": 0}
+    results = [None] * n
+    errors = []
+    t_start = time.perf_counter()
+
+    def worker():
+        ctx = make_ctx()
+        while True:
+            with cond:
+                while True:
+                    if st["next"] >= n or errors:
+                        return
+                    i = order[st["next"]]
+                    wait = arr[i] - (time.perf_counter() - t_start)
+                    fits = st["inflight"] == 0 or st["bytes"] + need[i] <= budget
+                    if wait <= 0 and fits:
+                        st["next"] += 1
+                        st["bytes"] += need[i]
+                        st["inflight"] += 1
+                        st["max_inflight"] = max(st["max_inflight"], st["inflight"])
+                        break
+                    cond.wait(timeout=min(max(wait, 1e-3), 0.05) if wait > 0 else 0.05)
+            begin = time.perf_counter() - t_start
+            try:
+                value = run(i, ctx)
+                results[i] = (value, begin, time.perf_counter() - t_start)
+            except BaseException as e:   # re-raised by the caller after the join
+                errors.append(e)
+            finally:
+                with cond:
+                    st["bytes"] -= need[i]
+                    st["inflight"] -= 1
+                    cond.notify_all()
+
+    threads = [threading.Thread(target=worker, daemon=True) for _ in range(max(1, slots))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    return results, {"makespan_s": time.perf_counter() - t_start, "max_inflight": st["max_inflight"]}
+
+
 def replay_latency(arrivals, service, load: float):
     """Latency (finish - arrival) of FIFO service on one server when the arrival times
     are rescaled to an offered rate of load / mean(service).  Returns (latency, rate)."""
@@ -314,15 +342,21 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--seed", type=int, default=100)
+    ap.add_argument("--slots", type=int, default=0,
+                    help="requests in flight at once (continuous batching); 0 serves one at a time")
     ap.add_argument("--records", action="store_true", help="include per-request records")
     args = ap.parse_args()
     import gpinputs
     reqs = gpinputs.serving_stream(args.requests, n_min=int(args.n_min), n_max=int(args.n_max), seed=args.seed,
                                    max_rhs=args.max_rhs, dims=tuple(int(v) for v in args.dims.split(",")),
                                    nus=tuple(float(v) for v in args.nus.split(",")))
-    out = Server(hbm_budget=args.budget_gb * 1e9, eps_target=args.eps).serve(reqs, load=args.load)
-    if not args.records:
-        out.pop("records")
+    srv = Server(hbm_budget=args.budget_gb * 1e9, eps_target=args.eps)
+    if args.slots > 0:
+        out = srv.serve_batched(reqs, load=args.load, slots=args.slots)
+    else:
+        out = srv.serve(reqs, load=args.load)
+        if not args.records:
+            out.pop("records")
     print(json.dumps(out))
 
 

@@ -1,10 +1,14 @@
-"""Host logic of the request loop (no GPU): the replayed FIFO clock and the admission
-by predicted footprint."""
+"""Host logic of the request loop (no GPU): the replayed FIFO clock, the admission by
+predicted footprint, and the continuous-batching scheduler (run_slots) driven by jobs
+that only sleep."""
 import numpy as np
 import pytest
 
 import gpinputs
-from paper_2407_03608_gb300.serving import EPS_LADDER, predicted_eps, replay_latency
+import threading
+import time
+
+from paper_2407_03608_gb300.serving import EPS_LADDER, predicted_eps, replay_latency, run_slots
 
 
 def test_idle_server_latency_is_service_time():
@@ -65,3 +69,84 @@ def test_short_length_scales_are_admitted_coarser(abi):
     req = gpinputs.serving_stream(8, n_min=1000, n_max=50_000, dims=(3,), nus=(1.5,), max_rhs=1)[0]
     eps = predicted_eps(abi, req, 120 * 10 ** 9, 1e-6)
     assert eps is not None and eps >= 1e-4
+
+
+class _Probe:
+    """Jobs that sleep and record how many run at once and how many bytes they hold."""
+
+    def __init__(self, need, dur=0.05):
+        self.need, self.dur = need, dur
+        self.lock = threading.Lock()
+        self.now = self.peak = self.bytes = self.peak_bytes = 0
+        self.ctx_made = 0
+
+    def make_ctx(self):
+        with self.lock:
+            self.ctx_made += 1
+            return self.ctx_made
+
+    def run(self, i, ctx):
+        with self.lock:
+            self.now += 1
+            self.bytes += self.need[i]
+            self.peak = max(self.peak, self.now)
+            self.peak_bytes = max(self.peak_bytes, self.bytes)
+        time.sleep(self.dur)
+        with self.lock:
+            self.now -= 1
+            self.bytes -= self.need[i]
+        return (i, ctx)
+
+
+def test_slots_bound_the_jobs_in_flight():
+    need = [1] * 7
+    p = _Probe(need)
+    res, info = run_slots(np.zeros(7), need, budget=100, slots=3, run=p.run, make_ctx=p.make_ctx)
+    assert p.peak == 3 and info["max_inflight"] == 3 and p.ctx_made == 3
+    assert [r[0][0] for r in res] == list(range(7))
+    # all at once: seven jobs of 50 ms on three slots take three rounds
+    assert 0.15 <= info["makespan_s"] < 0.15 + 0.5
+
+
+def test_memory_gate_holds_the_budget():
+    need = [60, 30, 30, 60, 10]
+    p = _Probe(need)
+    res, info = run_slots(np.zeros(5), need, budget=100, slots=4, run=p.run, make_ctx=p.make_ctx)
+    assert p.peak_bytes <= 100 and info["max_inflight"] >= 2
+    assert all(r is not None for r in res)
+
+
+def test_a_job_larger_than_the_budget_runs_alone():
+    need = [150, 10, 10]
+    p = _Probe(need)
+    res, info = run_slots(np.zeros(3), need, budget=100, slots=3, run=p.run, make_ctx=p.make_ctx)
+    starts = [r[1] for r in res]
+    ends = [r[2] for r in res]
+    assert min(starts[1:]) >= ends[0] - 1e-3        # the others waited for it to finish
+    assert info["max_inflight"] == 2
+
+
+def test_jobs_start_in_arrival_order_and_not_before_arriving():
+    arrivals = np.array([0.20, 0.0, 0.10, 0.10])
+    need = [1] * 4
+    p = _Probe(need, dur=0.01)
+    res, _ = run_slots(arrivals, need, budget=100, slots=2, run=p.run, make_ctx=p.make_ctx)
+    starts = np.array([r[1] for r in res])
+    assert np.all(starts >= arrivals - 1e-3)
+    order = np.argsort(starts, kind="stable")
+    assert list(order) in ([1, 2, 3, 0], [1, 3, 2, 0])
+
+
+def test_a_failing_job_is_reraised_and_stops_admission():
+    ran = []
+
+    def run(i, ctx):
+        ran.append(i)
+        if i == 1:
+            raise RuntimeError("job 1 failed")
+        time.sleep(0.01)
+        return i
+
+    with pytest.raises(RuntimeError, match="job 1 failed"):
+        run_slots(np.arange(6) * 0.02, [1] * 6, budget=100, slots=1, run=run)
+    assert ran == [0, 1]
