@@ -356,3 +356,55 @@ def test_planted_wrong_ghat_exponent_is_caught(monkeypatch):
     p = _params_1d(sig, n_t=30, n_s=10, M=300)
     assert np.max(np.abs(ktilde.dense(w.points, wp, sig, p) - ktilde.dense_poisson(w.points, wp, sig, p))) > \
         10 * ktilde.grid_tail_bound(wp, sig, p)
+
+
+# Each planted mistake below is caught by one of the pins above, which is called as it
+# stands and must fail.
+def test_planted_unscaled_sigma_mapping_is_caught(monkeypatch):
+    # sigma = l instead of l / sqrt(2)
+    monkeypatch.setattr(kernel, "paper_fields",
+                        lambda s, l, d: (np.asarray(s) * (2 * np.pi) ** (d / 4) * np.asarray(l) ** (d / 2),
+                                         np.asarray(l, dtype=np.float64)))
+    with pytest.raises(AssertionError):
+        test_scale_mapping_equals_paciorek_form()
+
+
+def test_planted_wrong_kernel_argument_is_caught(monkeypatch):
+    # phi(|x - y| / sqrt(sigma_x^2 + sigma_y^2)) evaluated at sqrt(2) times the argument
+    orig = kernel.phi
+    monkeypatch.setattr(kernel, "phi", lambda r, nu: orig(np.sqrt(2.0) * r, nu))
+    with pytest.raises(AssertionError):
+        test_stationary_special_case(1.5)
+
+
+def test_planted_wrong_chi_is_caught(monkeypatch):
+    # chi(t) = e^t / sqrt(nu) instead of e^{t/2} / sqrt(nu) (Eq. maternpres)
+    monkeypatch.setattr(quadrature, "chi_matern", lambda t, nu: np.exp(np.asarray(t, dtype=np.float64)) / np.sqrt(nu))
+    with pytest.raises(AssertionError):
+        test_schoenberg_integral_reproduces_matern(1.5)
+
+
+def test_planted_off_by_one_chebyshev_nodes_is_caught(monkeypatch):
+    # cos(pi k / (N_sigma + 1)): the last node misses sigma_min
+    def bad(smin, smax, n):
+        k = np.arange(n + 1)
+        return (np.cos(np.pi * k / (n + 1)) + 1.0) / 2.0 * (smax - smin) + smin
+    monkeypatch.setattr(chebyshev, "nodes", bad)
+    with pytest.raises(AssertionError):
+        test_chebyshev_nodes_and_lagrange_basis()
+
+
+def test_planted_reversed_channel_index_is_caught(monkeypatch):
+    # w_k(x) paired with the node sigma_{N_sigma - k}: the channels no longer match G^_k
+    orig = chebyshev.w_k
+    monkeypatch.setattr(chebyshev, "w_k", lambda w, sigma, nd, d: orig(w, sigma, nd, d)[:, ::-1])
+    with pytest.raises(AssertionError):
+        test_ktilde_converges_to_k_theorem_main()
+
+
+def test_planted_missing_grid_weight_is_caught(monkeypatch):
+    # v~_j = v_j, dropping the (dw)^d of Eq. (Ktilde)
+    orig = ktilde.a_tensor
+    monkeypatch.setattr(ktilde, "a_tensor", lambda p: orig(p) / p.dw ** p.d)
+    with pytest.raises(AssertionError):
+        test_ktilde_steps_equal_literal_definition_and_are_psd()
