@@ -284,6 +284,15 @@ int gp_posterior_mean_noalloc(gp_plan_t plan, const double* alpha, const double*
 int gp_profile_enable(gp_plan_t plan, int on);
 int gp_profile_read(gp_plan_t plan, double* ms_avg, long long* count);
 
+/* The library's own row kernels inside the two transform phases of the same
+ * recording (App. D: the row half of each 2-D FFT), as average milliseconds per
+ * matvec: ms_avg[0] of phase [1] (forward) and ms_avg[1] of phase [3] (inverse).
+ * The rest of each phase is cuFFT (the column transforms in d = 2).  Plans whose
+ * transforms are cuFFT alone give 0; the 1-D row transforms, which use no cuFFT,
+ * give the whole phase.  It waits for the last recorded matvec.
+ * Errors: GP_EINVAL, GP_ECUDA. */
+int gp_profile_read_rows(gp_plan_t plan, double* ms_avg);
+
 /* Copy the plan's chosen hyperparameters and sizes into *info. */
 int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info);
 

@@ -33,7 +33,8 @@ STATUS_NAMES = {0: "GP_OK", -1: "GP_EINVAL", -2: "GP_ENOMEM", -3: "GP_ECUDA", -4
 
 #: every symbol include/gpnufft.h declares
 EXPORTED = ["gp_plan_opts_default", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined",
-            "gp_posterior_mean", "gp_posterior_mean_noalloc", "gp_posterior_variance", "gp_profile_enable", "gp_profile_read", "gp_plan_info_get", "gp_destroy", "gp_last_error",
+            "gp_posterior_mean", "gp_posterior_mean_noalloc", "gp_posterior_variance", "gp_profile_enable",
+            "gp_profile_read", "gp_profile_read_rows", "gp_plan_info_get", "gp_destroy", "gp_last_error",
             "gp_version", "gp_tile_candidates", "gp_plan_params"]
 
 
@@ -102,6 +103,8 @@ def _load():
     lib.gp_profile_enable.restype = ctypes.c_int
     lib.gp_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     lib.gp_profile_read.restype = ctypes.c_int
+    lib.gp_profile_read_rows.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.gp_profile_read_rows.restype = ctypes.c_int
     lib.gp_plan_info_get.argtypes = [vp, ctypes.POINTER(gp_plan_info)]
     lib.gp_plan_info_get.restype = ctypes.c_int
     lib.gp_destroy.argtypes = [vp]
@@ -266,6 +269,13 @@ def gp_profile_read(plan):
     cnt = ctypes.c_longlong()
     check(LIB.gp_profile_read(plan, ms, ctypes.byref(cnt)))
     return list(ms), cnt.value
+
+
+def gp_profile_read_rows(plan):
+    """Average ms per matvec of the library's own row kernels in [fft_fwd, fft_inv]."""
+    ms = (ctypes.c_double * 2)()
+    check(LIB.gp_profile_read_rows(plan, ms))
+    return list(ms)
 
 
 def gp_plan_info_get(plan) -> dict:

@@ -868,6 +868,7 @@ int gp_profile_enable(gp_plan_t plan, int on) {
     if (on) {
       p->prof.harvest();
       for (double& a : p->prof.acc) a = 0.0;
+      for (double& a : p->prof.acc_rows) a = 0.0;
       p->prof.count = 0;
     }
     p->prof.on = on != 0;
@@ -885,6 +886,19 @@ int gp_profile_read(gp_plan_t plan, double* ms_avg, long long* count) {
     long long n = p->prof.count;
     for (int q = 0; q < 5; ++q) ms_avg[q] = n ? p->prof.acc[q] / n : 0.0;
     if (count) *count = n;
+    return GP_OK;
+  });
+}
+
+int gp_profile_read_rows(gp_plan_t plan, double* ms_avg) {
+  return guarded([&]() {
+    Plan* p = as_plan(plan);
+    bind_device(*p);
+    GPN_CHECK(ms_avg != nullptr, GP_EINVAL, "null ms_avg");
+    p->prof.harvest();
+    check_device_status(*p, nullptr);
+    long long n = p->prof.count;
+    for (int q = 0; q < 2; ++q) ms_avg[q] = n ? p->prof.acc_rows[q] / n : 0.0;
     return GP_OK;
   });
 }

@@ -614,10 +614,12 @@ void tr3_forward(Plan& plan, int R, cudaStream_t st) {
   cufftHandle h = plan.t3_plan(R);
   if (plan.precision == GP_FP32) {
     rows_run<float>(plan, false, plan.fx, R, st);
+    prof_mark(plan, 0, st);
     GPN_CUFFT3(cufftSetStream(h, st));
     GPN_CUFFT3(cufftExecC2C(h, (cufftComplex*)plan.fx, (cufftComplex*)plan.fy, CUFFT_FORWARD));
   } else {
     rows_run<double>(plan, false, plan.fx, R, st);
+    prof_mark(plan, 0, st);
     GPN_CUFFT3(cufftSetStream(h, st));
     GPN_CUFFT3(cufftExecZ2Z(h, (cufftDoubleComplex*)plan.fx, (cufftDoubleComplex*)plan.fy, CUFFT_FORWARD));
   }
@@ -641,9 +643,11 @@ void tr3_inverse(Plan& plan, int R, cudaStream_t st) {
   GPN_CUFFT3(cufftSetStream(h, st));
   if (plan.precision == GP_FP32) {
     GPN_CUFFT3(cufftExecC2C(h, (cufftComplex*)plan.fz, (cufftComplex*)plan.fy, CUFFT_INVERSE));
+    prof_mark(plan, 1, st);
     rows_run<float>(plan, true, plan.fy, R, st);
   } else {
     GPN_CUFFT3(cufftExecZ2Z(h, (cufftDoubleComplex*)plan.fz, (cufftDoubleComplex*)plan.fy, CUFFT_INVERSE));
+    prof_mark(plan, 1, st);
     rows_run<double>(plan, true, plan.fy, R, st);
   }
 }

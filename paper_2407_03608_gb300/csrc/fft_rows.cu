@@ -294,6 +294,7 @@ void forward_impl(Plan& plan, int R, cudaStream_t st) {
   const int rows = plan.geom.d == 2 ? plan.row_hi - plan.row_lo : 1;
   k_row_r2c<T><<<dim3(rows, a.CR), fft_threads(a.L), smem, st>>>(a);
   GPN_CUDA(cudaGetLastError());
+  prof_mark(plan, 0, st);
   if (plan.geom.d == 2) {
     cufftHandle hdl = plan.col_plan(R);
     GPN_CUFFT2(cufftSetStream(hdl, st));
@@ -341,6 +342,7 @@ void inverse_impl(Plan& plan, int R, cudaStream_t st) {
       GPN_CUFFT2(cufftExecZ2Z(hdl, (cufftDoubleComplex*)plan.fz, (cufftDoubleComplex*)plan.fy, CUFFT_INVERSE));
     W = (const typename Cplx<T>::type*)plan.fy;
   }
+  prof_mark(plan, 1, st);
   const int h = 1 << a.L;
   const size_t smem = sizeof(typename Cplx<T>::type) * h;
   GPN_CUDA(cudaFuncSetAttribute(k_row_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

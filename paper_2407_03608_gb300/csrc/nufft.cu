@@ -130,8 +130,10 @@ cufftHandle Plan::inv_plan(int R) {
 }
 
 void run_fft_forward(Plan& plan, int R, cudaStream_t st) {
+  // the row-kernel paths mark between their rows and cuFFT's columns themselves
   if (plan.tr3) return tr3_forward(plan, R, st);
   if (plan.rowfft) return rowfft_forward(plan, R, st);
+  prof_mark(plan, 0, st);                          // all of the phase is cuFFT
   cufftHandle h = plan.fwd_plan(R);
   GPN_CUFFT(cufftSetStream(h, st));
   if (plan.precision == GP_FP32)
@@ -149,6 +151,11 @@ void run_fft_inverse(Plan& plan, int R, cudaStream_t st) {
     GPN_CUFFT(cufftExecC2R(h, (cufftComplex*)plan.spec, (cufftReal*)plan.grid_out));
   else
     GPN_CUFFT(cufftExecZ2D(h, (cufftDoubleComplex*)plan.spec, (cufftDoubleReal*)plan.grid_out));
+  prof_mark(plan, 1, st);
+}
+
+void prof_mark(Plan& plan, int which, cudaStream_t st) {
+  if (plan.prof.in_matvec) GPN_CUDA(cudaEventRecord(plan.prof.mid[which], st));
 }
 
 void PhaseProfile::harvest() {
@@ -159,6 +166,11 @@ void PhaseProfile::harvest() {
     GPN_CUDA(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
     acc[q] += ms;
   }
+  float ms = 0.f;
+  GPN_CUDA(cudaEventElapsedTime(&ms, ev[1], mid[0]));
+  acc_rows[0] += ms;
+  GPN_CUDA(cudaEventElapsedTime(&ms, mid[1], ev[4]));
+  acc_rows[1] += ms;
   ++count;
   pending = false;
 }
@@ -166,6 +178,7 @@ void PhaseProfile::harvest() {
 void PhaseProfile::destroy() {
   if (!created) return;
   for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& e : mid) cudaEventDestroy(e);
   created = false;
 }
 
@@ -176,9 +189,11 @@ void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, i
     pf.harvest();
     if (!pf.created) {
       for (auto& e : pf.ev) GPN_CUDA(cudaEventCreate(&e));
+      for (auto& e : pf.mid) GPN_CUDA(cudaEventCreate(&e));
       pf.created = true;
     }
     GPN_CUDA(cudaEventRecord(pf.ev[0], st));
+    pf.in_matvec = true;
   }
   launch_spread(plan, alpha_sorted, R, st);
   if (rec) GPN_CUDA(cudaEventRecord(pf.ev[1], st));
@@ -190,6 +205,7 @@ void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, i
   if (rec) GPN_CUDA(cudaEventRecord(pf.ev[4], st));
   launch_interp(plan, plan.pts, alpha_sorted, shift, out_sorted, R, st);
   if (rec) {
+    pf.in_matvec = false;
     GPN_CUDA(cudaEventRecord(pf.ev[5], st));
     pf.pending = true;
   }

@@ -47,8 +47,13 @@ struct PhaseProfile {
   bool on = false;
   bool created = false;
   bool pending = false;
+  bool in_matvec = false;   // between the first and last event of a recorded matvec
   cudaEvent_t ev[6];
+  // mid[0]: the forward phase's own row kernels end and its cuFFT part begins;
+  // mid[1]: the inverse phase's cuFFT part ends and its own row kernels begin
+  cudaEvent_t mid[2];
   double acc[5] = {0, 0, 0, 0, 0};
+  double acc_rows[2] = {0, 0};   // ms in the transform phases' own row kernels
   long long count = 0;
   void harvest();   // fold the pending event set into acc (waits for it)
   void destroy();
@@ -236,6 +241,9 @@ void run_fft_inverse(Plan& plan, int R, cudaStream_t st);
 // Pruned transforms (fft_rows.cu).
 bool rowfft_supported(int d, long long nf, size_t rs);
 void build_twiddles(Plan& plan);
+// Record the transform-phase boundary `which` (0 forward, 1 inverse) of the matvec
+// being profiled; nothing when no matvec is being recorded.
+void prof_mark(Plan& plan, int which, cudaStream_t st);
 void rowfft_forward(Plan& plan, int R, cudaStream_t st);
 void rowfft_diag(Plan& plan, int R, cudaStream_t st);
 void rowfft_inverse(Plan& plan, int R, cudaStream_t st);
