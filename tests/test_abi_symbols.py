@@ -59,6 +59,9 @@ def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
 
 
 def test_struct_layout_matches_header(lib, tmp_path):
+    # every field of the ctypes mirrors, at the offset gcc gives the header's field
+    fields = [(sname, f[0]) for sname in ("gp_plan_opts", "gp_plan_info") for f in getattr(lib, sname)._fields_]
+    body = "".join("  F(%s, %s)\n" % sf for sf in fields)
     prog = tmp_path / "layout.c"
     prog.write_text(r'''
 #include <stdio.h>
@@ -68,9 +71,7 @@ def test_struct_layout_matches_header(lib, tmp_path):
 int main(void) {
   printf("gp_plan_opts %zu\n", sizeof(gp_plan_opts));
   printf("gp_plan_info %zu\n", sizeof(gp_plan_info));
-  F(gp_plan_opts, set) F(gp_plan_opts, M) F(gp_plan_opts, box_lo) F(gp_plan_opts, nf) F(gp_plan_opts, transform) F(gp_plan_opts, max_bytes)
-  F(gp_plan_info, M) F(gp_plan_info, nf) F(gp_plan_info, transform) F(gp_plan_info, box_hi) F(gp_plan_info, est_err_alias)
-  F(gp_plan_info, bytes_resident) F(gp_plan_info, max_rhs)
+''' + body + r'''
   return 0;
 }
 ''')
@@ -79,6 +80,7 @@ int main(void) {
     out = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)], text=True).split("\n") if line)
     assert int(out["gp_plan_opts"]) == ctypes.sizeof(lib.gp_plan_opts)
     assert int(out["gp_plan_info"]) == ctypes.sizeof(lib.gp_plan_info)
+    assert len(out) == 2 + len(fields)
     for key, val in out.items():
         if "." in key:
             s, m = key.split(".")
