@@ -85,3 +85,53 @@ int main(void) {
         if "." in key:
             s, m = key.split(".")
             assert getattr(getattr(lib, s), m).offset == int(val), key
+
+
+def test_every_entry_point_refuses_a_null_plan(lib):
+    L = lib.LIB
+    calls = {
+        "gp_matvec": lambda: L.gp_matvec(None, None, None, 1, 0.0, None),
+        "gp_cg_solve": lambda: L.gp_cg_solve(None, None, None, 1, 0.0, 1e-6, 10, None, None, None),
+        "gp_cg_solve_refined": lambda: L.gp_cg_solve_refined(None, None, None, None, 1, 0.0, 1e-8, 1e-4, 5, 10,
+                                                             None, None, None),
+        "gp_posterior_mean": lambda: L.gp_posterior_mean(None, None, None, 1, None, None, None, None),
+        "gp_posterior_mean_noalloc": lambda: L.gp_posterior_mean_noalloc(None, None, None, 1, None, None, None, None),
+        "gp_posterior_variance": lambda: L.gp_posterior_variance(None, None, 1, 0.1, 1e-6, 10, None, None, None),
+        "gp_profile_enable": lambda: L.gp_profile_enable(None, 1),
+        "gp_profile_read": lambda: L.gp_profile_read(None, None, None),
+        "gp_profile_read_rows": lambda: L.gp_profile_read_rows(None, None),
+        "gp_plan_info_get": lambda: L.gp_plan_info_get(None, None),
+    }
+    plan_taking = [n for n in declared_functions() if n not in
+                   ("gp_plan", "gp_plan_opts_default", "gp_plan_params", "gp_tile_candidates", "gp_destroy",
+                    "gp_last_error", "gp_version")]
+    assert sorted(calls) == sorted(plan_taking)
+    for name, call in calls.items():
+        assert call() == lib.GP_EINVAL, name
+        assert L.gp_last_error() == b"null plan", name
+
+
+def test_plan_arguments_are_checked_before_any_device_work(lib):
+    h = ctypes.c_void_p()
+    x = (ctypes.c_double * 4)(0.1, 0.2, 0.3, 0.4)
+    one = (ctypes.c_double * 4)(1, 1, 1, 1)
+    o = lib.default_opts()
+    bad = [
+        (x, 4, 4, one, one, 1.5, 1e-6, o, "d must be"),
+        (x, 0, 1, one, one, 1.5, 1e-6, o, "N must be"),
+        (x, 4, 1, one, one, -1.0, 1e-6, o, "nu must be"),
+        (x, 4, 1, one, one, 1.5, 0.5, o, "eps must be"),
+        (x, 4, 1, one, one, 1.5, 0.0, o, "eps must be"),
+        (x, 4, 1, one, one, 1.5, 1e-6, lib.default_opts(precision=7), "precision"),
+        (x, 4, 1, one, one, 1.5, 1e-6, lib.default_opts(max_rhs=5000), "max_rhs"),
+        (x, 4, 1, one, one, 1.5, 1e-6, lib.default_opts(autotune=9), "autotune"),
+    ]
+    for pts, n, d, fa, fb, nu, eps, opts, msg in bad:
+        st = _plan_call(lib, h, pts, n, d, fa, fb, nu, eps, opts)
+        assert st == lib.GP_EINVAL, msg
+        assert msg.encode() in lib.LIB.gp_last_error(), (msg, lib.LIB.gp_last_error())
+        assert h.value is None
+
+
+def _plan_call(lib, h, pts, n, d, fa, fb, nu, eps, opts):
+    return lib.LIB.gp_plan(ctypes.byref(h), pts, n, d, fa, fb, nu, eps, ctypes.byref(opts), None)
