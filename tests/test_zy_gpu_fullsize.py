@@ -1,0 +1,78 @@
+"""Parity at the full benchmark sizes, with the plans bench.py times.
+
+The workloads are too large for the dense oracle, so the GPU matvec is compared with
+the oracle's exact rows of K alpha (Eq. nonstat2, direct sums over all N points) on
+seeded samples of rows:
+  * 2-D clustered, N = 1e6, Matern 3/2, eps = 1e-6, FP32 plan: sampled rows within the
+    FP32 bar 1e-4 (measured about 1e-6), and the whole vector within 1e-4 of the FP64
+    plan on the same parameters;
+  * 3-D uniform, N = 2e6, Matern 5/2, eps = 1e-6, FP32 plan (about 100 GB resident):
+    sampled rows within 1e-4.
+The file sorts after the other GPU tests so that their plans are gone when these large
+ones are built; a test is skipped when the device has less free memory than it needs.
+"""
+import gc
+
+import numpy as np
+import pytest
+import torch
+
+import gpinputs
+from oracle import kernel as okern
+from oracle import rows as orows
+
+pytestmark = pytest.mark.gpu
+
+
+def _free_after_cleanup():
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return torch.cuda.mem_get_info()[0]
+
+
+def _rows_error(w, got, n_rows, seed):
+    wp, sig = okern.paper_fields(w.s, w.l, w.d)
+    idx = np.random.default_rng(seed).choice(w.N, size=n_rows, replace=False)
+    ref = orows.rows(w.points, wp, sig, w.nu, w.alpha, idx)
+    return float(np.linalg.norm(got[idx] - ref) / np.linalg.norm(ref))
+
+
+def _plan(gpn, w, precision, **kw):
+    dev = torch.device("cuda")
+    return gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
+                    torch.from_numpy(w.l).to(dev), nu=w.nu, eps=w.eps, precision=precision, **kw)
+
+
+def test_two_dimensional_benchmark_workload(gpn):
+    if _free_after_cleanup() < 48e9:
+        pytest.skip("needs about 40 GB of free device memory")
+    w = gpinputs.config_2d(1_000_000, 1.5)
+    a = torch.from_numpy(w.alpha).cuda()
+    p32 = _plan(gpn, w, gpn.GP_FP32)
+    try:
+        got = p32.matvec(a).cpu().numpy()
+        p64 = _plan(gpn, w, gpn.GP_FP64, **p32.matched_opts())
+        try:
+            got64 = p64.matvec(a).cpu().numpy()
+        finally:
+            p64.close()
+    finally:
+        p32.close()
+    e_rows = _rows_error(w, got, 1024, seed=31)
+    assert e_rows <= 1e-4, e_rows
+    e_64 = float(np.linalg.norm(got - got64) / np.linalg.norm(got64))
+    assert e_64 <= 1e-4, e_64
+
+
+def test_three_dimensional_workload(gpn):
+    if _free_after_cleanup() < 110e9:
+        pytest.skip("needs about 100 GB of free device memory")
+    w = gpinputs.config_3d(2_000_000)
+    p32 = _plan(gpn, w, gpn.GP_FP32)
+    try:
+        got = p32.matvec(torch.from_numpy(w.alpha).cuda()).cpu().numpy()
+    finally:
+        p32.close()
+    e_rows = _rows_error(w, got, 256, seed=32)
+    assert e_rows <= 1e-4, e_rows
