@@ -19,7 +19,7 @@ simple distribution) at the sizes of the five benchmark workloads.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import Dict, List, Optional
+from typing import Dict, List
 
 import numpy as np
 

@@ -4,7 +4,6 @@ Each test ties one oracle function to a closed form, an independent library
 routine, a quadrature of the defining integral, an invariant, or a number the
 paper prints.  No GPU.
 """
-import math
 
 import numpy as np
 import pytest
