@@ -1,0 +1,43 @@
+"""Reruns of the paper's matvec experiments in two and three dimensions (Sec. 6.1),
+in the setup of tests/test_gpu_paper_experiments.py (x ~ U[-1,1]^d, w = 1, sigma(x) =
+(prod cos(pi x_i) + 2)/6, the paper's dw and t-range, NUFFTs at eps_NUFFT/10 = 1e-7),
+against the exact K alpha on sampled rows.
+
+* Fig. matvec2d (Matern nu = 3/2, d = 2, reference point N_t = 20, N_sigma = 20,
+  M = 200; the values are lost): each coarser parameter raises the error.  The oracle's
+  K~ (exact NUDFT, N = 300) puts the reference point at 4e-4 to 7e-4 and N_t = 10,
+  N_sigma = 3, M = 60 at 1.7e-2, 5.6e-3 and 1.6e-2.
+* Figs. matvec2d-gauss, matvec3d-gauss and the text after Fig. matvecN-gauss (SE,
+  d = 2 with N_sigma = 26, M = 140; d = 3 with N_sigma = 16, M = 50): an accuracy of
+  roughly 1e-7 whatever N.  The oracle puts the approximation error of K~ at 2e-15
+  (d = 2) and 3e-10 (d = 3), so what is measured is the NUFFT tolerance, two transforms
+  of d dimensions at 1e-7 each; the bars are 1e-6 (d = 2) and 2e-6 (d = 3).  Coarser
+  N_sigma or M (oracle: 8e-5 and 5e-4 in d = 2 at N_sigma = 6, M = 15; 1.6e-4 and 1.4e-3
+  in d = 3 at N_sigma = 6, M = 15) must raise the error well above that floor.
+"""
+import pytest
+
+from test_gpu_paper_experiments import run
+
+pytestmark = pytest.mark.gpu
+
+
+def test_e2_matern_2d_ablation_lowers_the_error(gpn):
+    base = dict(n_t=20, n_sigma=20, M=200)
+    ref = run(gpn, 2, 1000, 1.5, **base)
+    assert ref <= 5e-3, ref
+    for key, coarse in (("n_t", 10), ("n_sigma", 3), ("M", 60)):
+        e = run(gpn, 2, 1000, 1.5, **dict(base, **{key: coarse}))
+        assert e > 3 * ref, (key, e, ref)
+
+
+@pytest.mark.parametrize("d,n_sigma,M,bar", [(2, 26, 140, 1e-6), (3, 16, 50, 2e-6)])
+def test_e4_e5_se_accuracy_independent_of_n(gpn, d, n_sigma, M, bar):
+    errs = [run(gpn, d, n, None, n_sigma, M, seed=s) for s, n in enumerate((1_000, 10_000, 100_000))]
+    assert max(errs) <= bar, errs
+    assert max(errs) <= 10 * min(errs), errs
+    for key, coarse in (("n_sigma", 6), ("M", 15)):
+        kw = dict(n_sigma=n_sigma, M=M)
+        kw[key] = coarse
+        e = run(gpn, d, 10_000, None, seed=1, **kw)
+        assert e > 30 * max(errs), (key, e, errs)
