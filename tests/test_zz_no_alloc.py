@@ -1,7 +1,8 @@
 """gp_posterior_mean_noalloc: the posterior mean (Eq. postmean) through the entry
 point whose scratch is a static device array, against gp_posterior_mean on the
-same plan.  Collected last so that it runs both after the other GPU tests and,
-when selected alone, in a fresh process where its first call does the set-up.
+same plan.  Collected after the tests of the other entry points so that it runs
+after them and, when selected alone, in a fresh process where its first call does
+the set-up.
 
 Tolerances (relative l2 against gp_posterior_mean): the two evaluate the same sum
 in another order, so FP64 <= 1e-12 and FP32 <= 1e-5.
