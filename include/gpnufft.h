@@ -187,7 +187,10 @@ void gp_plan_opts_default(gp_plan_opts* opts);
  * adds the exact diagonal defect.  Device memory: about info.bytes_resident, checked
  * against opts->max_bytes before the large allocations.
  * Errors: GP_EINVAL (d not 1..3, N < 1, nu <= 0, eps out of range, non-positive
- * scale, inconsistent overrides), GP_ENOMEM, GP_ECUDA, GP_ECUFFT. On error *out is NULL. */
+ * scale, inconsistent overrides), GP_EUNSUPPORTED (no kernel configuration for these
+ * sizes, e.g. no spreading tile fits in shared memory for the kernel width, or the
+ * memory-lean step 3 with transform 2), GP_ENOMEM, GP_ECUDA, GP_ECUFFT.
+ * On error *out is NULL. */
 int gp_plan(gp_plan_t* out, const double* points, long long N, int d, const double* field_a,
             const double* field_b, double nu, double eps, const gp_plan_opts* opts, void* cuda_stream);
 
