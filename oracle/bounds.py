@@ -6,8 +6,6 @@ Definition epcheb / Lemma interp: for all x,
 k = 0, which is the reading used here.)
 
 Definition eptrap: e^(-alpha t_max) + e^(nu t_min) + e^(-(1-delta) pi^2 / dt).
-
-Definition epF: lambda^d e^(-[2 pi rho_min M dw]^2) + e^(-[1/(4 rho_max dw)]^2).
 """
 from __future__ import annotations
 
@@ -35,7 +33,3 @@ def eps_trap(nu: float, alpha: float, delta: float, t_min: float, t_max: float, 
     dt = (t_max - t_min) / n_t
     return float(np.exp(-alpha * t_max) + np.exp(nu * t_min) + np.exp(-(1.0 - delta) * np.pi ** 2 / dt))
 
-
-def eps_F(lam: float, d: int, rho_min: float, rho_max: float, M: int, dw: float) -> float:
-    return float(lam ** d * np.exp(-(2.0 * np.pi * rho_min * M * dw) ** 2)
-                 + np.exp(-(1.0 / (4.0 * rho_max * dw)) ** 2))

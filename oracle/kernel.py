@@ -67,11 +67,6 @@ def solve_cholesky(K, eta2: float, y):
     return scipy.linalg.cho_solve(c, y)
 
 
-def posterior_mean(Kqx, alpha):
-    """mu(x_q) = sum_n alpha_n K(x_q, x_n), Eq. (postmean)."""
-    return Kqx @ alpha
-
-
 def cg(apply_A, y, rtol: float, maxit: int):
     """Plain conjugate gradients for a symmetric positive definite operator.
 

@@ -114,6 +114,23 @@ def test_trapezoid_converges_and_halves_end_weights():
     assert np.allclose(tau, [0.5, 1, 1, 1, 0.5])
 
 
+def test_trapezoid_error_follows_lemma_dt():
+    # tails negligible: the error is the discretisation term of Definition eptrap,
+    # e^{-(1 - delta) pi^2 / dt}; the integrand is analytic in the strip |Im t| < pi/2,
+    # so no rule can beat e^{-pi^2 / dt}
+    nu, delta = 1.5, 0.2
+    t_min, t_max = np.log(special.gammaincinv(nu, 1e-16)), np.log(special.gammainccinv(nu, 1e-16))
+    r = np.linspace(0, 10, 400)
+    inv_dt, log_err = [], []
+    for n in (8, 12, 16, 20, 24, 28, 32):
+        err = np.max(np.abs(quadrature.phi_from_quadrature(r, nu, t_min, t_max, n) - matern.phi_matern(r, nu)))
+        assert err <= 10 * bounds.eps_trap(nu, 10.0, delta, t_min, t_max, n), n
+        inv_dt.append(n / (t_max - t_min))
+        log_err.append(np.log(err))
+    rate = -np.polyfit(inv_dt, log_err, 1)[0]
+    assert (1 - delta) * np.pi ** 2 <= rate <= 1.05 * np.pi ** 2, rate
+
+
 # ---------------------------------------------- Gaussian identities (App. B, App. E)
 def test_gaussian_product_integral_appendix_b():
     a, b, x, y = 0.13, 0.21, 0.05, 0.31
