@@ -110,3 +110,30 @@ def test_invalid_arguments(abi):
         assert e.value.status == abi.GP_EINVAL
     abi.gp_plan_params(2, 10, 1.5, 1e-3, 0.01, 0.02, [0, 0], [1, 1], o)   # clears the error message
     assert abi.LIB.gp_last_error() == b""
+
+
+# The parameters chosen for eps against the oracle's K~ (Eq. Ktilde written out densely)
+# and the dense K (Eq. nonstat2): Theorem main's entrywise error relative to
+# sqrt(K_ii K_jj) must meet eps, and the choice should not overshoot it by much (each
+# stage of the selector aims at a share of eps).
+@pytest.mark.parametrize("d,nu,eps", [(1, 1.5, 1e-3), (1, 1.5, 1e-5), (1, 2.5, 1e-7), (1, None, 1e-5),
+                                      (2, 1.5, 1e-2), (2, 2.5, 1e-3)])
+def test_chosen_parameters_meet_eps_against_the_oracle(abi, d, nu, eps):
+    import gpinputs
+    from oracle import kernel as okern
+    from oracle import ktilde
+    w = gpinputs.config_1d(200) if d == 1 else gpinputs.config_2d(120)
+    X = w.points
+    wp, sig = okern.paper_fields(w.s, w.l, d)
+    fam = abi.GP_SE if nu is None else abi.GP_MATERN
+    o = abi.default_opts(precision=abi.GP_FP64, family=fam)
+    i = abi.gp_plan_params(d, X.shape[0], 1.0 if nu is None else nu, eps, float(sig.min()), float(sig.max()),
+                           [float(v) for v in X.min(0)], [float(v) for v in X.max(0)], o)
+    nu_o = np.inf if nu is None else nu
+    p = ktilde.Params(d, nu_o, i["t_min"], i["t_max"], i["n_t"], i["sigma_lo"], i["sigma_hi"], i["n_sigma"],
+                      int(i["M"]), i["dw"])
+    Kt = ktilde.dense(X, wp, sig, p)
+    K = okern.kernel_dense(X, wp, sig, nu_o)
+    dg = np.sqrt(np.diag(K))
+    err = float(np.max(np.abs(K - Kt) / np.outer(dg, dg)))
+    assert eps / 30 <= err <= eps, (err, {k: i[k] for k in ("n_t", "n_sigma", "M")})
