@@ -116,7 +116,7 @@ def test_invalid_arguments(abi):
 # and the dense K (Eq. nonstat2): Theorem main's entrywise error relative to
 # sqrt(K_ii K_jj) must meet eps, and the choice should not overshoot it by much (each
 # stage of the selector aims at a share of eps).
-@pytest.mark.parametrize("d,nu,eps", [(1, 1.5, 1e-3), (1, 1.5, 1e-5), (1, 2.5, 1e-7), (1, None, 1e-5),
+@pytest.mark.parametrize("d,nu,eps", [(1, 0.5, 1e-3), (1, 1.5, 1e-3), (1, 1.5, 1e-5), (1, 2.5, 1e-7), (1, None, 1e-5),
                                       (2, 1.5, 1e-2), (2, 2.5, 1e-3)])
 def test_chosen_parameters_meet_eps_against_the_oracle(abi, d, nu, eps):
     import gpinputs
