@@ -137,3 +137,27 @@ def test_chosen_parameters_meet_eps_against_the_oracle(abi, d, nu, eps):
     dg = np.sqrt(np.diag(K))
     err = float(np.max(np.abs(K - Kt) / np.outer(dg, dg)))
     assert eps / 30 <= err <= eps, (err, {k: i[k] for k in ("n_t", "n_sigma", "M")})
+
+
+# Stage 1 (Lemma dt) of the host selector against the oracle's quadrature: the tails sit
+# where the regularised incomplete gamma puts eps/12 (scipy), the selector's estimate
+# of the trapezoid error equals the oracle's sup |phi - sum_j tau_j u_j e^{-r^2/(2 chi_j^2)}|,
+# it meets eps/4, and one node fewer would not.
+@pytest.mark.parametrize("nu", [1.5, 2.5, 3.2])
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_stage_one_quadrature_matches_the_oracle(abi, nu, eps):
+    from scipy import special
+    from oracle import matern, quadrature
+    i = abi.gp_plan_params(1, 1000, nu, eps, 0.01, 0.02, [0.0], [1.0], abi.default_opts())
+    assert special.gammainc(nu, np.exp(i["t_min"])) == pytest.approx(eps / 12, rel=1e-6)
+    assert special.gammaincc(nu, np.exp(i["t_max"])) == pytest.approx(eps / 12, rel=1e-6)
+    r = np.concatenate([np.linspace(0, 2, 4001), np.linspace(2, 60, 4001)])
+
+    def sup_err(n_t):
+        q = quadrature.phi_from_quadrature(r, nu, i["t_min"], i["t_max"], n_t)
+        return float(np.max(np.abs(q - matern.phi_matern(r, nu))))
+
+    e = sup_err(i["n_t"])
+    assert e == pytest.approx(i["est_err_t"], rel=1e-2)
+    assert e <= eps / 4
+    assert sup_err(i["n_t"] - 1) > 0.98 * eps / 4
