@@ -161,3 +161,30 @@ def test_stage_one_quadrature_matches_the_oracle(abi, nu, eps):
     assert e == pytest.approx(i["est_err_t"], rel=1e-2)
     assert e <= eps / 4
     assert sup_err(i["n_t"] - 1) > 0.98 * eps / 4
+
+
+# Stage 3 (Lemma stage3) of the host selector, recomputed with the oracle's trapezoid
+# table (tau_j, u(t_j), chi_j): the truncation estimate d sum_j tau_j u_j erfc(2 pi
+# sigma_lo chi_j M dw) meets eps/4 and one mode fewer would not; the alias estimate
+# d sum_j tau_j u_j exp(-(1/dw - L)^2 / (4 sigma_hi^2 chi_j^2)) meets eps/8, with L the
+# widest side of the box.
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("nu,eps", [(1.5, 1e-4), (2.5, 1e-7)])
+def test_stage_three_estimates_match_the_oracle_tables(abi, d, nu, eps):
+    from scipy import special
+    from oracle import quadrature
+    lo, hi = [0.0] * d, [1.0, 0.8, 0.6][:d]
+    i = abi.gp_plan_params(d, 10_000, nu, eps, 0.02, 0.05, lo, hi, abi.default_opts())
+    t, _, chi, tau = quadrature.trapezoid_table(nu, d, i["t_min"], i["t_max"], i["n_t"])
+    wu = tau * quadrature.u_matern(t, nu)
+
+    def trunc(M):
+        return d * float(np.sum(wu * special.erfc(2 * np.pi * i["sigma_lo"] * chi * M * i["dw"])))
+
+    assert trunc(i["M"]) == pytest.approx(i["est_err_trunc"], rel=1e-6)
+    assert trunc(i["M"]) <= eps / 4 < trunc(i["M"] - 1)
+    L = max(i["box_hi"][a] - i["box_lo"][a] for a in range(d))
+    gap = 1.0 / i["dw"] - L
+    alias = d * float(np.sum(wu * np.exp(-gap ** 2 / (4 * i["sigma_hi"] ** 2 * chi ** 2))))
+    assert alias == pytest.approx(i["est_err_alias"], rel=1e-6)
+    assert alias <= eps / 8
