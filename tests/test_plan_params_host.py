@@ -188,3 +188,40 @@ def test_stage_three_estimates_match_the_oracle_tables(abi, d, nu, eps):
     alias = d * float(np.sum(wu * np.exp(-gap ** 2 / (4 * i["sigma_hi"] ** 2 * chi ** 2))))
     assert alias == pytest.approx(i["est_err_alias"], rel=1e-6)
     assert alias <= eps / 8
+
+
+# Stage 2 (Lemma sigma) of the host selector with the oracle's Chebyshev nodes and
+# Lagrange basis (product formula; the library evaluates the barycentric form): the
+# sup over sigma_x, sigma_y and rho of the interpolated normalised Gaussian product,
+#   |sum_kl P_k(s_x) P_l(s_y) c_kl e^{-rho^2/(2 s_kl)} - c(s_x, s_y) e^{-rho^2/(2 (s_x^2 + s_y^2))}|
+#   / (s_x s_y / 2)^{d/2},   c(a, b) = (a^2 b^2 / (a^2 + b^2))^{d/2},
+# sampled on grids that contain the selector's (so it can only find more), bounds the
+# selector's estimate from above, stays near eps/4 at the chosen N_sigma and exceeds
+# eps/4 with one node fewer.
+def _stage2_sup(d, lo, hi, n_sigma, ns=47, nr=95):
+    from oracle import chebyshev
+    nd = chebyshev.nodes(lo, hi, n_sigma)
+    sv = lo + (hi - lo) * np.arange(ns) / (ns - 1)
+    P = chebyshev.lagrange(sv, nd)                                    # (ns, C)
+    a2, b2 = nd[:, None] ** 2, nd[None, :] ** 2
+    ckl, skl = (a2 * b2 / (a2 + b2)) ** (d / 2), a2 + b2
+    x2, y2 = sv[:, None] ** 2, sv[None, :] ** 2
+    cxy, sxy = (x2 * y2 / (x2 + y2)) ** (d / 2), x2 + y2
+    norm = (0.5 * sv[:, None] * sv[None, :]) ** (d / 2)
+    worst = 0.0
+    for rho in 12.0 * hi * np.arange(nr) / (nr - 1):
+        approx = P @ (ckl * np.exp(-rho ** 2 / (2 * skl))) @ P.T
+        exact = cxy * np.exp(-rho ** 2 / (2 * sxy))
+        worst = max(worst, float(np.max(np.abs(approx - exact) / norm)))
+    return worst
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("smin,smax,eps", [(0.02, 0.03, 1e-4), (0.02, 0.04, 1e-7), (0.01, 0.04, 1e-6)])
+def test_stage_two_estimate_against_the_oracle_basis(abi, d, smin, smax, eps):
+    i = abi.gp_plan_params(d, 10_000, 1.5, eps, smin, smax, [0.0] * d, [1.0] * d, abi.default_opts())
+    n, lo, hi = i["n_sigma"], i["sigma_lo"], i["sigma_hi"]
+    sup = _stage2_sup(d, lo, hi, n)
+    assert sup >= i["est_err_sigma"] * (1 - 1e-9)
+    assert i["est_err_sigma"] <= eps / 4 and sup <= 1.5 * eps / 4
+    assert _stage2_sup(d, lo, hi, n - 1) > eps / 4
