@@ -1,8 +1,8 @@
 """CPU oracle for the non-stationary Matern GP matvec and solve (TEST INFRASTRUCTURE).
 
 This package is test infrastructure, not part of the library.  Only the test
-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
-import or run it.  The CUDA library never calls it, and it shares no code,
+suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg and reference arm of
+``bench.py`` may import or run it.  The CUDA library never calls it, and it shares no code,
 table or constant with the CUDA library: both sides take their inputs from the
 seeded generators in ``gpinputs`` and nothing else.
 
@@ -29,6 +29,8 @@ Modules:
   ktilde      Fourier tables, tensor A (Remark rem:step3), exact K~ matvec, Poisson K~
   nudft       type-1 / type-2 non-uniform DFTs (App. D)
   rows        exact sampled rows of K alpha (C, OpenMP) for large N
-  bounds      the error bounds of Sec. 5 (Lemmas dt, interp; Definition epF)
+  bounds      the error quantities of Sec. 5 (Definition eptrap; Lemma interp)
+  diagcorr    the exact diagonal K~_ii and the diagonal-corrected matvec (an extension)
+  variance    posterior variance at the training points and its probe estimator (an extension)
 """
 from . import matern, kernel, quadrature, chebyshev, nudft, ktilde, bounds, rows  # noqa: F401
