@@ -163,7 +163,9 @@ int gp_tile_candidates(int d, int n_channels, int precision, int width, int* til
  * step-3 form).  info->bytes_resident is the estimate of the large allocations that
  * gp_plan checks against max_bytes.  The free device memory is not known here, so the
  * memory-lean step 3 is predicted only from max_bytes or an explicit opts->step3.
- * Errors: GP_EINVAL, GP_EUNSUPPORTED as for gp_plan. */
+ * Errors: GP_EINVAL, GP_EUNSUPPORTED as for gp_plan; GP_ENOMEM when the host-side
+ * tables of the chosen parameters (C (N_t+1) (M+1) doubles) do not fit in host memory,
+ * as for nu = 1/2 at tight eps, where M grows like eps^(-1/(2 nu)) (Sec. 5.4). */
 int gp_plan_params(int d, long long N, double nu, double eps, double sigma_min, double sigma_max,
                    const double* box_lo, const double* box_hi, const gp_plan_opts* opts, gp_plan_info* info);
 
