@@ -352,9 +352,15 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   GPN_CHECK(d == 1 || (h.tile * rs) % 16 == 0, GP_EINVAL,
             "tile must be a multiple of 16 bytes of grid values (4 in FP32, 2 in FP64) for d >= 2");
   GPN_CHECK(h.tile >= h.width - 1 && h.tile >= 1, GP_EINVAL, "tile must be >= kernel width - 1");
-  Tables local;
-  Tables& t = tb ? *tb : local;
-  build_tables(h, t);
+  // the host tables hold C (N_t + 1) (M + 1) doubles of per-dimension factors (and
+  // M + 1 values of psi^); refuse them before allocating when M is out of reach (nu = 1/2
+  // at tight eps), and build them only for a plan, not for a parameter query
+  const long long J = h.family == GP_SE ? 1 : (long long)h.n_t + 1;
+  const double table_bytes = 8.0 * (double)C * (double)J * (double)(h.M + 1);
+  GPN_CHECK(table_bytes <= kHostTableMax, GP_ENOMEM,
+            "host tables of " + std::to_string((long long)table_bytes) + " bytes for M = " + std::to_string(h.M) +
+                " exceed the limit of " + std::to_string((long long)kHostTableMax));
+  if (tb) build_tables(h, *tb);
 
   long long G = 1;
   for (int q = 0; q < d; ++q) G *= h.nf;
@@ -376,7 +382,7 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   ps.S = S;
   ps.nfreq = nfreq;
   ps.a_bytes = (long long)(C * (C + 1) / 2) * nfreq * (long long)rs;
-  ps.lean_bytes = (long long)t.vt.size() * (h.M + 1) * lean_channel_pitch(C, rs) * (long long)rs;
+  ps.lean_bytes = J * (h.M + 1) * lean_channel_pitch(C, rs) * (long long)rs;
   // the large allocations: spreading and interpolation grids, spectra or the pruned
   // transforms' column buffers, per-point data and the nine work vectors
   const long long CR = (long long)C * max_rhs;

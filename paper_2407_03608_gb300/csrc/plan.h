@@ -192,6 +192,7 @@ void build_a_tensor(Plan& plan, cudaStream_t st);
 constexpr size_t kInterpSmemBudget = size_t(96) << 10;   // target when sizing channel chunks
 constexpr size_t kInterpSmemMax = size_t(200) << 10;      // one staged channel must fit
 constexpr size_t kSpreadSmemMax = size_t(160) << 10;      // shared tile of one spreading channel chunk
+constexpr double kHostTableMax = 32e9;                     // bytes of plan-time host tables
 int spread_pitch(int d, int tile);
 size_t spread_smem_bytes(int d, int tile, int C, size_t rs, int width);
 int interp_pitch(int d, int tile, int width, size_t rs);

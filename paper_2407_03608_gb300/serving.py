@@ -80,9 +80,16 @@ def predicted_footprint(abi, req, eps: float) -> int:
 def predicted_eps(abi, req, budget: int, eps_target: float) -> Optional[float]:
     """The finest eps of the ladder (from eps_target) at which the request's FP64 and FP32
     plans together are predicted to fit `budget` bytes.  None when even the coarsest level
-    does not fit."""
+    does not fit.  A level whose parameters are out of reach (gp_plan_params reports
+    GP_ENOMEM or GP_EUNSUPPORTED, as for nu = 1/2 at tight eps) does not fit."""
     for eps in [e for e in EPS_LADDER if e >= eps_target * (1 - 1e-12)]:
-        if predicted_footprint(abi, req, eps) <= budget:
+        try:
+            need = predicted_footprint(abi, req, eps)
+        except abi.GPError as e:
+            if e.status in (abi.GP_ENOMEM, abi.GP_EUNSUPPORTED):
+                continue
+            raise
+        if need <= budget:
             return eps
     return None
 
@@ -190,8 +197,9 @@ class Server:
         arr = np.zeros(len(requests)) if arrivals is None else np.asarray(arrivals, dtype=np.float64)
         need = []
         for req in requests:
-            eps = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
-            need.append(predicted_footprint(self.gpn.abi, req, max(eps, self.eps_target)))
+            eps = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target)
+            # a request that fits no level is admitted alone (it holds the whole budget)
+            need.append(self.budget if eps is None else predicted_footprint(self.gpn.abi, req, eps))
         device = torch.cuda.current_device()
 
         def make_stream():

@@ -150,3 +150,15 @@ def test_a_failing_job_is_reraised_and_stops_admission():
     with pytest.raises(RuntimeError, match="job 1 failed"):
         run_slots(np.arange(6) * 0.02, [1] * 6, budget=100, slots=1, run=run)
     assert ran == [0, 1]
+
+
+def test_levels_out_of_reach_are_skipped(abi):
+    # nu = 1/2 in 1-D: M grows like eps^-1, and at eps = 1e-6 the plan's host tables
+    # alone would take hundreds of GB; admission moves on to a coarser level
+    req = gpinputs.serving_stream(1, n_min=1000, n_max=1000, dims=(1,), nus=(0.5,), max_rhs=1, seed=3)[0]
+    with pytest.raises(abi.GPError) as e:
+        from paper_2407_03608_gb300.serving import predicted_footprint
+        predicted_footprint(abi, req, 1e-6)
+    assert e.value.status == abi.GP_ENOMEM
+    eps = predicted_eps(abi, req, 10 ** 13, 1e-6)
+    assert eps is not None and eps > 1e-6
