@@ -135,3 +135,16 @@ def test_plan_arguments_are_checked_before_any_device_work(lib):
 
 def _plan_call(lib, h, pts, n, d, fa, fb, nu, eps, opts):
     return lib.LIB.gp_plan(ctypes.byref(h), pts, n, d, fa, fb, nu, eps, ctypes.byref(opts), None)
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    # the product path has no host implementation: without a CUDA device a plan cannot
+    # be built, and the call says why
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import numpy as np
+    import paper_2407_03608_gb300 as gpn
+    with pytest.raises(gpn.GPError) as e:
+        gpn.Plan(np.linspace(0, 1, 50).reshape(-1, 1), np.ones(50), np.full(50, 0.05), nu=1.5, eps=1e-4)
+    assert e.value.status == lib.GP_ECUDA
