@@ -148,3 +148,20 @@ def test_no_cpu_fallback_without_a_gpu(lib):
     with pytest.raises(gpn.GPError) as e:
         gpn.Plan(np.linspace(0, 1, 50).reshape(-1, 1), np.ones(50), np.full(50, 0.05), nu=1.5, eps=1e-4)
     assert e.value.status == lib.GP_ECUDA
+
+
+def test_importing_without_the_built_library_raises(tmp_path):
+    # a copy of the package's Python files with no _build directory: the import fails
+    # loudly instead of falling back to anything
+    import shutil
+    import sys
+    pkg = os.path.join(ROOT, "paper_2407_03608_gb300")
+    dst = tmp_path / "paper_2407_03608_gb300"
+    dst.mkdir()
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(pkg, f), dst / f)
+    r = subprocess.run([sys.executable, "-c", "import paper_2407_03608_gb300"], cwd=str(tmp_path),
+                       capture_output=True, text=True, env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libgpnufft.so is not built" in r.stderr
