@@ -100,12 +100,12 @@ class _Probe:
 
 def test_slots_bound_the_jobs_in_flight():
     need = [1] * 7
-    p = _Probe(need)
+    p = _Probe(need, dur=0.1)
     res, info = run_slots(np.zeros(7), need, budget=100, slots=3, run=p.run, make_ctx=p.make_ctx)
     assert p.peak == 3 and info["max_inflight"] == 3 and p.ctx_made == 3
     assert [r[0][0] for r in res] == list(range(7))
-    # all at once: seven jobs of 50 ms on three slots take three rounds
-    assert 0.15 <= info["makespan_s"] < 0.15 + 0.5
+    # all at once: seven jobs of 100 ms on three slots take three rounds
+    assert 0.3 <= info["makespan_s"] < 0.3 + 1.0
 
 
 def test_memory_gate_holds_the_budget():
@@ -118,7 +118,7 @@ def test_memory_gate_holds_the_budget():
 
 def test_a_job_larger_than_the_budget_runs_alone():
     need = [150, 10, 10]
-    p = _Probe(need)
+    p = _Probe(need, dur=0.2)
     res, info = run_slots(np.zeros(3), need, budget=100, slots=3, run=p.run, make_ctx=p.make_ctx)
     starts = [r[1] for r in res]
     ends = [r[2] for r in res]
