@@ -57,7 +57,7 @@ typedef enum {
   GP_ENOTCONV = -5,      /* CG reached maxit before rtol; alpha holds the last iterate */
   GP_EBREAKDOWN = -6,    /* CG breakdown: p^T A p <= 0 or not finite                 */
   GP_ETIMEOUT = -7,      /* a bounded device wait ran out                            */
-  GP_EUNSUPPORTED = -8   /* configuration not supported by this build                */
+  GP_EUNSUPPORTED = -8   /* a configuration the kernels do not support               */
 } gp_status;
 
 enum { GP_FP64 = 0, GP_FP32 = 1 };                 /* arithmetic of spread/FFT/step 3/interp */
