@@ -254,7 +254,7 @@ int gp_posterior_variance(gp_plan_t plan, const double* probes, int R, double et
 #define GP_NOALLOC_MAX_QUERIES 32768
 
 /* gp_posterior_mean without any device allocation.  The paper has no counterpart:
- * it is a serving form of the same result (Eq. postmean), for callers that must not
+ * it computes the same result as gp_posterior_mean, for callers that must not
  * allocate while they run, such as a serving loop that shares the device with
  * other streams (cudaFree synchronises the whole device) or a process that has
  * committed the device memory up front.
@@ -267,8 +267,9 @@ int gp_posterior_variance(gp_plan_t plan, const double* probes, int R, double et
  *   Queries outside the plan box or sigma range get mu = NaN and the call
  *   returns GP_EINVAL after the others are written.
  * The first call on each device does a one-time set-up (it looks up the device
- * address of the static array, with the plan's device current); make that first
- * call before any stream capture begins.  The static array is shared by all calls
+ * address of the static array and the SM count, with the plan's device current;
+ * again after the device's context has been reset); make that first call before
+ * any stream capture begins.  The static array is shared by all calls
  * on a device: calls whose GPU work overlaps (other streams, other host threads,
  * other plans) race on it.  The call waits for its stream before returning.
  * Errors: GP_EINVAL, GP_ECUDA, GP_ECUFFT, GP_ETIMEOUT. */

@@ -836,7 +836,8 @@ int gp_posterior_mean_noalloc(gp_plan_t plan, const double* alpha, const double*
               "Nq must be in [1, " + std::to_string(GP_NOALLOC_MAX_QUERIES) +
                   "]: the static scratch of gp_posterior_mean_noalloc holds that many queries");
     const int d = p->h.d;
-    unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch(p->device));
+    const NoAllocScratch ns = noalloc_scratch(p->device);
+    unsigned char* scratch = static_cast<unsigned char*>(ns.ptr);
     unsigned* bad = reinterpret_cast<unsigned*>(scratch);
     double* stage = reinterpret_cast<double*>(scratch + kNoAllocHeaderBytes);
     double* sx = stage;
@@ -854,7 +855,7 @@ int gp_posterior_mean_noalloc(gp_plan_t plan, const double* alpha, const double*
     run_fft_forward(*p, 1, st);
     launch_diag(*p, 1, st);
     run_fft_inverse(*p, 1, st);
-    launch_query_interp(*p, x, fa, fb, Nq, o.dev, bad, st);
+    launch_query_interp(*p, x, fa, fb, Nq, o.dev, bad, ns.sms, st);
     if (o.host) GPN_CUDA(cudaMemcpyAsync(o.host, o.dev, sizeof(double) * Nq, cudaMemcpyDeviceToHost, st));
     check_device_status(*p, st);  // also waits for the stream
     GPN_CUDA(cudaMemcpyAsync(p->host_status, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

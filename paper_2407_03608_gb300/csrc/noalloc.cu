@@ -15,6 +15,8 @@
 //
 // The scratch is shared by every call on a device: calls whose GPU work overlaps
 // (other streams, other host threads, other plans) race on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "kernels.h"
@@ -27,7 +29,27 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+// per device: the context the address was looked up in, the address and the SM count
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+NoAllocScratch g_scratch[kMaxDevices] = {};
+
+// The current context, through the runtime's driver entry point (the library does not
+// link libcuda).  A reset device gets a new primary context, which loads the module, and
+// so the array, again.
+CUcontext current_context() {
+  using GetCtx = CUresult (*)(CUcontext*);
+  static GetCtx get = nullptr;
+  if (!get) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    GPN_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q));
+    GPN_CHECK(q == cudaDriverEntryPointSuccess && fn, GP_ECUDA, "cuCtxGetCurrent unavailable");
+    get = (GetCtx)fn;
+  }
+  CUcontext c = nullptr;
+  GPN_CHECK(get(&c) == CUDA_SUCCESS, GP_ECUDA, "cuCtxGetCurrent failed");
+  return c;
+}
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
@@ -91,6 +113,9 @@ __global__ void __launch_bounds__(256) k_query_interp(QueryArgs<T> a) {
       ok = ok && isfinite(xa) && xa >= a.box_lo[q] && xa <= a.box_hi[q];
       const double g = (xa - a.centre[q]) * a.inv_h + a.half_nf;
       const double l0d = ceil(g - a.half_w);
+      // The plan centres the box on the grid with a margin of at least width/2 + 2 cells
+      // per side, so for a query inside the box the support lies inside the grid and
+      // this test never rejects it; it only guards the grid reads below.
       ok = ok && l0d >= 0.0 && l0d + W <= (double)a.nf;
       l0[q] = ok ? (long long)l0d : 0;
       xi[q] = ok ? (T)(g - l0d) : T(0);
@@ -178,7 +203,7 @@ void launch_d(const QueryArgs<T>& a, int blocks, cudaStream_t st) {
 
 template <typename T>
 void query_impl(Plan& plan, const double* x, const double* fa, const double* fb, long long nq, double* mu,
-                unsigned* bad, cudaStream_t st) {
+                unsigned* bad, int sms, cudaStream_t st) {
   const Hyper& h = plan.h;
   const GridGeom& g = plan.geom;
   QueryArgs<T> a{};
@@ -211,7 +236,8 @@ void query_impl(Plan& plan, const double* x, const double* fa, const double* fb,
   a.beta = es_beta_arg<T>(g.beta);
   a.inv_halfw = (T)(2.0 / g.width);
   a.bad = bad;
-  const int blocks = (int)std::min<long long>((nq + 7) / 8, 152 * 8);
+  // eight warps (queries) a block; at most eight blocks an SM, the rest by the grid-stride loop
+  const int blocks = (int)std::min<long long>((nq + 7) / 8, (long long)sms * 8);
   switch (h.d) {
     case 1: launch_d<T, 1>(a, blocks, st); break;
     case 2: launch_d<T, 2>(a, blocks, st); break;
@@ -222,25 +248,30 @@ void query_impl(Plan& plan, const double* x, const double* fa, const double* fb,
 
 }  // namespace
 
-void* noalloc_scratch(int device) {
+NoAllocScratch noalloc_scratch(int device) {
   GPN_CHECK(device >= 0 && device < kMaxDevices, GP_EUNSUPPORTED, "device ordinal beyond the scratch table");
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_ptr[device]) {
-    // the caller has made `device` current; the symbol's address is per device
-    void* p = nullptr;
-    GPN_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_ptr[device] = p;
+  // the caller has made `device` current; the symbol's address is per device (and per
+  // context: after a reset of the device it is looked up again)
+  const CUcontext ctx = current_context();
+  if (!g_scratch[device].ptr || g_scratch_ctx[device] != ctx) {
+    NoAllocScratch s{};
+    GPN_CUDA(cudaGetSymbolAddress(&s.ptr, g_noalloc_scratch));
+    GPN_CUDA(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, device));
+    GPN_CHECK(s.ptr && s.sms > 0, GP_ECUDA, "no device address or SM count for the static scratch");
+    g_scratch[device] = s;
+    g_scratch_ctx[device] = ctx;
   }
-  return g_scratch_ptr[device];
+  return g_scratch[device];
 }
 
 void launch_query_interp(Plan& plan, const double* x, const double* fa, const double* fb, long long nq, double* mu,
-                         unsigned* bad, cudaStream_t st) {
+                         unsigned* bad, int sms, cudaStream_t st) {
   if (nq == 0) return;
   if (plan.precision == GP_FP32)
-    query_impl<float>(plan, x, fa, fb, nq, mu, bad, st);
+    query_impl<float>(plan, x, fa, fb, nq, mu, bad, sms, st);
   else
-    query_impl<double>(plan, x, fa, fb, nq, mu, bad, st);
+    query_impl<double>(plan, x, fa, fb, nq, mu, bad, sms, st);
 }
 
 }  // namespace gpn

@@ -228,13 +228,19 @@ void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, d
 constexpr size_t kNoAllocHeaderBytes = 256;
 constexpr size_t kNoAllocScratchBytes =
     kNoAllocHeaderBytes + sizeof(double) * (kMaxDim + 3) * (size_t)GP_NOALLOC_MAX_QUERIES;
-// Device address of the scratch on `device` (must be current); looked up on the
-// first call per device.
-void* noalloc_scratch(int device);
+// Device address of the scratch on `device` (must be current) and the device's SM
+// count; looked up on the first call per device (again after the device's context
+// was reset).
+struct NoAllocScratch {
+  void* ptr;
+  int sms;
+};
+NoAllocScratch noalloc_scratch(int device);
 // mu_q = sum_k w_k(x_q) beta_k(x_q) from plan.grid_out (right-hand side 0), one warp
 // per query; *bad counts queries outside the box or sigma range (mu is NaN there).
+// sms: the device's SM count (sizes the grid).
 void launch_query_interp(Plan& plan, const double* x, const double* fa, const double* fb, long long nq, double* mu,
-                         unsigned* bad, cudaStream_t st);
+                         unsigned* bad, int sms, cudaStream_t st);
 // FFTs of the fine grids (forward R2C, inverse C2R), batched over C * R.
 void run_fft_forward(Plan& plan, int R, cudaStream_t st);
 void run_fft_inverse(Plan& plan, int R, cudaStream_t st);

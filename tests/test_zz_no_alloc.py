@@ -94,3 +94,32 @@ def test_noalloc_flags_queries_outside_the_box(gpn):
     # the counter is cleared on the next call
     abi.gp_posterior_mean_noalloc(plan._h, alpha, xq, sq, lq, mu)
     assert rel(mu, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_noalloc_queries_on_the_box_corners(gpn, d):
+    # queries exactly on box_lo and box_hi in every axis (all 2^d corners plus the face
+    # centres): their supports reach furthest towards the grid edge
+    from paper_2407_03608_gb300 import abi
+    w, plan, _, _, _ = _case(gpn, d, gpn.GP_FP64, 1, seed=30 + d)
+    info = plan.info
+    lo = np.array(info["box_lo"][:d])
+    hi = np.array(info["box_hi"][:d])
+    corners = np.array([[hi[q] if (c >> q) & 1 else lo[q] for q in range(d)] for c in range(2 ** d)])
+    faces = []
+    for q in range(d):
+        for v in (lo[q], hi[q]):
+            f = 0.5 * (lo + hi)
+            f[q] = v
+            faces.append(f)
+    xq = np.vstack([corners, np.array(faces)])
+    fields = {1: gpinputs.fields_1d, 2: gpinputs.fields_2d, 3: gpinputs.fields_3d}[d]
+    sq, lq = fields(xq)
+    lq = np.clip(lq, np.sqrt(2) * info["sigma_lo"], np.sqrt(2) * info["sigma_hi"])
+    for seed in (51, 52):
+        alpha = gpinputs.random_alpha(w.N, 1, seed=seed)
+        ref = plan.posterior_mean(alpha, xq, sq, lq)
+        mu = np.full(len(xq), np.nan)
+        abi.gp_posterior_mean_noalloc(plan._h, alpha, xq, sq, lq, mu)
+        assert np.all(np.isfinite(mu))
+        assert rel(mu, ref) <= 1e-12
