@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the side measurements (config 1 latency, batched R, config 3, served solves)")
     ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="a fixed workload for profilers: build one plan (--d, --n, --eps, --precision, "
+                         "--transform) and run --matvecs matvecs, nothing else")
+    ap.add_argument("--d", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--matvecs", type=int, default=4)
+    ap.add_argument("--transform", type=int, default=0)
     return ap.parse_args()
 
 
@@ -542,9 +548,35 @@ def side_measurements(args, dev):
     return res
 
 
+def run_profile_case(args):
+    """One plan and a few matvecs of it, so that an ncu launch filter (-k, -s, -c) sees
+    only the plan build and the matvec kernels.  d = 2: the clustered workload (Matern
+    3/2); d = 3: uniform in the unit cube (Matern 5/2)."""
+    import torch
+    import gpinputs
+    import paper_2407_03608_gb300 as gpn
+    w = gpinputs.config_2d(args.n, 1.5) if args.d == 2 else gpinputs.config_3d(args.n)
+    dev = torch.device("cuda", 0)
+    prec = gpn.GP_FP32 if args.precision == "fp32" else gpn.GP_FP64
+    plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
+                    torch.from_numpy(w.l).to(dev), nu=w.nu, eps=args.eps, precision=prec,
+                    transform=args.transform)
+    a = torch.from_numpy(w.alpha).to(dev)
+    out = None
+    for _ in range(args.matvecs):
+        out = plan.matvec(a)
+    torch.cuda.synchronize()
+    i = plan.info
+    print({k: i[k] for k in ("nf", "M", "n_sigma", "kernel_width", "tile", "transform")}, float(out.norm()))
+    plan.close()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return

@@ -156,9 +156,11 @@ typedef struct gp_plan_info {
 int gp_tile_candidates(int d, int n_channels, int precision, int width, int* tiles, int max_tiles);
 
 /* The parameters a plan would get, and its device footprint, without building it and
- * without a GPU (host only).  The data enter through their ranges: sigma_min..sigma_max,
- * the paper's horizontal scale sigma(x_i) (sigma = l / sqrt(2) for GP_PARAMS_SCALES),
- * and the box box_lo[q] <= x_iq <= box_hi[q] (d entries each).  The hyperparameters are
+ * without a GPU (host only).  The data enter through their ranges: scale_min..scale_max,
+ * the range of the second per-point field in opts->param_mode (the length l(x_i) for
+ * GP_PARAMS_SCALES, the default; the paper's horizontal scale sigma(x_i) for
+ * GP_PARAMS_PAPER; the library maps l to sigma = l / sqrt(2) as gp_plan does), and the
+ * box box_lo[q] <= x_iq <= box_hi[q] (d entries each).  The hyperparameters are
  * chosen as gp_plan chooses them (Sec. 5.4 recipe, fine grid, tile, transform mode,
  * step-3 form).  info->bytes_resident is the estimate of the large allocations that
  * gp_plan checks against max_bytes.  The free device memory is not known here, so the
@@ -166,7 +168,7 @@ int gp_tile_candidates(int d, int n_channels, int precision, int width, int* til
  * Errors: GP_EINVAL, GP_EUNSUPPORTED as for gp_plan; GP_ENOMEM when the host-side
  * tables of the chosen parameters (C (N_t+1) (M+1) doubles) do not fit in host memory,
  * as for nu = 1/2 at tight eps, where M grows like eps^(-1/(2 nu)) (Sec. 5.4). */
-int gp_plan_params(int d, long long N, double nu, double eps, double sigma_min, double sigma_max,
+int gp_plan_params(int d, long long N, double nu, double eps, double scale_min, double scale_max,
                    const double* box_lo, const double* box_hi, const gp_plan_opts* opts, gp_plan_info* info);
 
 /* Fill opts with the defaults (all zero except max_rhs = 1). */

@@ -292,13 +292,14 @@ def gp_version() -> str:
     return LIB.gp_version().decode()
 
 
-def gp_plan_params(d: int, N: int, nu: float, eps: float, sigma_min: float, sigma_max: float, box_lo, box_hi,
+def gp_plan_params(d: int, N: int, nu: float, eps: float, scale_min: float, scale_max: float, box_lo, box_hi,
                    opts: gp_plan_opts = None) -> dict:
-    """The plan gp_plan would build for data with these ranges, and its footprint (no GPU)."""
+    """The plan gp_plan would build for data with these ranges, and its footprint (no GPU).
+    scale_min/scale_max: range of the second field in opts.param_mode (l, or the paper's sigma)."""
     lo = (ctypes.c_double * 3)(*[float(v) for v in box_lo] + [0.0] * (3 - len(box_lo)))
     hi = (ctypes.c_double * 3)(*[float(v) for v in box_hi] + [0.0] * (3 - len(box_hi)))
     info = gp_plan_info()
-    check(LIB.gp_plan_params(int(d), int(N), float(nu), float(eps), float(sigma_min), float(sigma_max), lo, hi,
+    check(LIB.gp_plan_params(int(d), int(N), float(nu), float(eps), float(scale_min), float(scale_max), lo, hi,
                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(info)))
     return info.as_dict()
 

@@ -910,20 +910,27 @@ int gp_profile_read_rows(gp_plan_t plan, double* ms_avg) {
   });
 }
 
-int gp_plan_params(int d, long long N, double nu, double eps, double sigma_min, double sigma_max,
+int gp_plan_params(int d, long long N, double nu, double eps, double scale_min, double scale_max,
                    const double* box_lo, const double* box_hi, const gp_plan_opts* opts, gp_plan_info* info) {
   return guarded([&]() {
     GPN_CHECK(info != nullptr && box_lo != nullptr && box_hi != nullptr, GP_EINVAL, "null info or box");
     GPN_CHECK(d >= 1 && d <= 3, GP_EINVAL, "d must be 1, 2 or 3");
     GPN_CHECK(N >= 1, GP_EINVAL, "N must be >= 1");
-    GPN_CHECK(sigma_min > 0.0 && sigma_max >= sigma_min && std::isfinite(sigma_max), GP_EINVAL,
-              "need 0 < sigma_min <= sigma_max");
+    GPN_CHECK(scale_min > 0.0 && scale_max >= scale_min && std::isfinite(scale_max), GP_EINVAL,
+              "need 0 < scale_min <= scale_max");
     for (int q = 0; q < d; ++q)
       GPN_CHECK(std::isfinite(box_lo[q]) && std::isfinite(box_hi[q]) && box_hi[q] >= box_lo[q], GP_EINVAL,
                 "bad point box");
     gp_plan_opts o;
     gp_plan_opts_default(&o);
     if (opts) o = *opts;
+    GPN_CHECK(o.param_mode == GP_PARAMS_SCALES || o.param_mode == GP_PARAMS_PAPER, GP_EINVAL,
+              "param_mode must be GP_PARAMS_SCALES or GP_PARAMS_PAPER");
+    // the range of the second field in the plan's parametrisation: the length l (sigma =
+    // l / sqrt(2), the same product gp_plan applies to every point) or sigma itself
+    const double kInvSqrt2 = 0.70710678118654752440;
+    const double sigma_min = o.param_mode == GP_PARAMS_SCALES ? scale_min * kInvSqrt2 : scale_min;
+    const double sigma_max = o.param_mode == GP_PARAMS_SCALES ? scale_max * kInvSqrt2 : scale_max;
     GPN_CHECK(o.family == GP_MATERN || o.family == GP_SE, GP_EINVAL, "family must be GP_MATERN or GP_SE");
     GPN_CHECK(o.family == GP_SE || (nu > 0.0 && std::isfinite(nu)), GP_EINVAL, "nu must be > 0");
     GPN_CHECK(eps > 0.0 && eps <= 0.1, GP_EINVAL, "eps must be in (0, 0.1]");

@@ -24,7 +24,10 @@ namespace gpn {
 namespace {
 constexpr double kPi = 3.14159265358979323846;
 
-// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+// Gauss-Legendre nodes and weights on [-1, 1]: the nodes are the roots of the Legendre
+// polynomial P_n, found by Newton's method from the asymptotic first guess
+// cos(pi (i + 3/4) / (n + 1/2)), with P_n and P_n' from the three-term (Bonnet) recurrence
+// (k P_k = (2k - 1) z P_{k-1} - (k - 1) P_{k-2}); the weights are 2 / ((1 - z^2) P_n'(z)^2).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);
@@ -273,7 +276,13 @@ double phi_radial(int family, double nu, double r) {
   return matern_phi(nu, r);
 }
 
-// Series for P(a,x) (x < a+1) and continued fraction for Q(a,x) (x >= a+1).
+// Regularised incomplete gamma functions P(a, x) and Q(a, x) = 1 - P(a, x), by the two
+// textbook expansions: for x < a + 1 the power series
+//   P(a, x) = e^{-x} x^a / Gamma(a) * sum_n x^n / (a (a+1) ... (a+n)),
+// and for x >= a + 1 the continued fraction of Legendre for Q(a, x),
+//   Q(a, x) = e^{-x} x^a / Gamma(a) * 1 / (x + 1 - a - 1 (1 - a) / (x + 3 - a - 2 (2 - a) / (x + 5 - a - ...))),
+// evaluated from the front by the modified Lentz method (Lentz 1976, with Thompson and
+// Barnett's guard against zero denominators).
 double gamma_p(double a, double x) {
   if (x <= 0.0) return 0.0;
   if (x < a + 1.0) {

@@ -67,11 +67,11 @@ def predicted_footprint(abi, req, eps: float) -> int:
     (gp_plan_params, no allocation)."""
     x = np.asarray(req.points, dtype=np.float64)
     N, d = x.shape
-    sig = np.asarray(req.l, dtype=np.float64) / np.sqrt(2.0)     # GP_PARAMS_SCALES: sigma = l / sqrt(2)
+    l = np.asarray(req.l, dtype=np.float64)                      # the plan's fields are (s, l)
     lo, hi = x.min(axis=0), x.max(axis=0)
     total = 0
     for prec in (abi.GP_FP64, abi.GP_FP32):
-        info = abi.gp_plan_params(d, N, req.nu, eps, float(sig.min()), float(sig.max()), lo, hi,
+        info = abi.gp_plan_params(d, N, req.nu, eps, float(l.min()), float(l.max()), lo, hi,
                                   abi.default_opts(precision=prec, max_rhs=_rhs(req)))
         total += int(info["bytes_resident"])
     return total

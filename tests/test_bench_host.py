@@ -16,9 +16,8 @@ def bench_plan():
     __graft_entry__.build()
     from paper_2407_03608_gb300 import abi
     w = gpinputs.config_2d(1_000_000, 1.5)
-    sig = w.l / np.sqrt(2.0)
     o = abi.default_opts(precision=abi.GP_FP32)
-    info = abi.gp_plan_params(2, w.N, w.nu, w.eps, float(sig.min()), float(sig.max()),
+    info = abi.gp_plan_params(2, w.N, w.nu, w.eps, float(w.l.min()), float(w.l.max()),
                               [float(v) for v in w.points.min(0)], [float(v) for v in w.points.max(0)], o)
     return w, info
 

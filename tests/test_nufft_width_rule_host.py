@@ -47,7 +47,8 @@ def abi():
                                            (1e-9, None, 728), (1e-7, None, 1164), (1e-9, None, 1164)])
 def test_selected_kernel_reaches_the_tolerance(abi, tol, upsamp, nf):
     set_bits = abi.GP_SET_NUFFT | (abi.GP_SET_NF if nf else 0)
-    o = abi.default_opts(precision=abi.GP_FP64, nufft_tol=tol, upsampfac=upsamp or 2.0, nf=nf or 0, set=set_bits)
+    o = abi.default_opts(precision=abi.GP_FP64, nufft_tol=tol, upsampfac=upsamp or 2.0, nf=nf or 0, set=set_bits,
+                         param_mode=abi.GP_PARAMS_PAPER)
     i = abi.gp_plan_params(1, 300, 1.5, 1e-3, 0.01, 0.03, [0.0], [1.0], o)
     M, width = int(i["M"]), int(i["kernel_width"])
     assert i["upsampfac"] == pytest.approx(i["nf"] / (2 * M + 1))

@@ -21,7 +21,8 @@ def smooth7(n):
 
 
 def params(abi, d, N, eps, smin, smax, nu=1.5, precision=1, **kw):
-    o = abi.default_opts(precision=precision, **kw)
+    # smin, smax: the paper's sigma
+    o = abi.default_opts(precision=precision, param_mode=abi.GP_PARAMS_PAPER, **kw)
     return abi.gp_plan_params(d, N, nu, eps, smin, smax, [0.0] * d, [1.0] * d, o)
 
 
@@ -58,10 +59,10 @@ def test_three_dimensional_grid_model(abi):
 def test_three_dimensional_nf_override_and_stride_rule(abi):
     smin, smax = 0.05 / np.sqrt(2), 0.10 / np.sqrt(2)
     base = params(abi, 3, 10_000, 1e-4, smin, smax, nu=2.5)
-    o = abi.default_opts(precision=abi.GP_FP32, nf=base["nf"] + 4, set=abi.GP_SET_NF)
+    o = abi.default_opts(precision=abi.GP_FP32, nf=base["nf"] + 4, set=abi.GP_SET_NF, param_mode=abi.GP_PARAMS_PAPER)
     i = abi.gp_plan_params(3, 10_000, 2.5, 1e-4, smin, smax, [0, 0, 0], [1, 1, 1], o)
     assert i["nf"] == base["nf"] + 4
-    o = abi.default_opts(precision=abi.GP_FP32, nf=base["nf"] + 2, set=abi.GP_SET_NF)
+    o = abi.default_opts(precision=abi.GP_FP32, nf=base["nf"] + 2, set=abi.GP_SET_NF, param_mode=abi.GP_PARAMS_PAPER)
     with pytest.raises(abi.GPError) as e:
         abi.gp_plan_params(3, 10_000, 2.5, 1e-4, smin, smax, [0, 0, 0], [1, 1, 1], o)
     assert e.value.status == abi.GP_EINVAL and "16-byte" in str(e.value)
@@ -126,7 +127,7 @@ def test_chosen_parameters_meet_eps_against_the_oracle(abi, d, nu, eps):
     X = w.points
     wp, sig = okern.paper_fields(w.s, w.l, d)
     fam = abi.GP_SE if nu is None else abi.GP_MATERN
-    o = abi.default_opts(precision=abi.GP_FP64, family=fam)
+    o = abi.default_opts(precision=abi.GP_FP64, family=fam, param_mode=abi.GP_PARAMS_PAPER)
     i = abi.gp_plan_params(d, X.shape[0], 1.0 if nu is None else nu, eps, float(sig.min()), float(sig.max()),
                            [float(v) for v in X.min(0)], [float(v) for v in X.max(0)], o)
     nu_o = np.inf if nu is None else nu
@@ -148,7 +149,7 @@ def test_chosen_parameters_meet_eps_against_the_oracle(abi, d, nu, eps):
 def test_stage_one_quadrature_matches_the_oracle(abi, nu, eps):
     from scipy import special
     from oracle import matern, quadrature
-    i = abi.gp_plan_params(1, 1000, nu, eps, 0.01, 0.02, [0.0], [1.0], abi.default_opts())
+    i = abi.gp_plan_params(1, 1000, nu, eps, 0.01, 0.02, [0.0], [1.0], abi.default_opts(param_mode=abi.GP_PARAMS_PAPER))
     assert special.gammainc(nu, np.exp(i["t_min"])) == pytest.approx(eps / 12, rel=1e-6)
     assert special.gammaincc(nu, np.exp(i["t_max"])) == pytest.approx(eps / 12, rel=1e-6)
     r = np.concatenate([np.linspace(0, 2, 4001), np.linspace(2, 60, 4001)])
@@ -174,7 +175,7 @@ def test_stage_three_estimates_match_the_oracle_tables(abi, d, nu, eps):
     from scipy import special
     from oracle import quadrature
     lo, hi = [0.0] * d, [1.0, 0.8, 0.6][:d]
-    i = abi.gp_plan_params(d, 10_000, nu, eps, 0.02, 0.05, lo, hi, abi.default_opts())
+    i = abi.gp_plan_params(d, 10_000, nu, eps, 0.02, 0.05, lo, hi, abi.default_opts(param_mode=abi.GP_PARAMS_PAPER))
     t, _, chi, tau = quadrature.trapezoid_table(nu, d, i["t_min"], i["t_max"], i["n_t"])
     wu = tau * quadrature.u_matern(t, nu)
 
@@ -219,9 +220,23 @@ def _stage2_sup(d, lo, hi, n_sigma, ns=47, nr=95):
 @pytest.mark.parametrize("d", [1, 2, 3])
 @pytest.mark.parametrize("smin,smax,eps", [(0.02, 0.03, 1e-4), (0.02, 0.04, 1e-7), (0.01, 0.04, 1e-6)])
 def test_stage_two_estimate_against_the_oracle_basis(abi, d, smin, smax, eps):
-    i = abi.gp_plan_params(d, 10_000, 1.5, eps, smin, smax, [0.0] * d, [1.0] * d, abi.default_opts())
+    i = abi.gp_plan_params(d, 10_000, 1.5, eps, smin, smax, [0.0] * d, [1.0] * d,
+                           abi.default_opts(param_mode=abi.GP_PARAMS_PAPER))
     n, lo, hi = i["n_sigma"], i["sigma_lo"], i["sigma_hi"]
     sup = _stage2_sup(d, lo, hi, n)
     assert sup >= i["est_err_sigma"] * (1 - 1e-9)
     assert i["est_err_sigma"] <= eps / 4 and sup <= 1.5 * eps / 4
     assert _stage2_sup(d, lo, hi, n - 1) > eps / 4
+
+
+def test_scale_range_is_taken_in_the_plans_parametrisation(abi):
+    # GP_PARAMS_SCALES (default): the range of the length l; the library maps it to the
+    # paper's sigma = l / sqrt(2), the same plan as passing sigma with GP_PARAMS_PAPER
+    lmin, lmax = 0.02, 0.04
+    a = abi.gp_plan_params(2, 100_000, 1.5, 1e-5, lmin, lmax, [0, 0], [1, 1], abi.default_opts(precision=abi.GP_FP32))
+    b = abi.gp_plan_params(2, 100_000, 1.5, 1e-5, lmin / np.sqrt(2), lmax / np.sqrt(2), [0, 0], [1, 1],
+                           abi.default_opts(precision=abi.GP_FP32, param_mode=abi.GP_PARAMS_PAPER))
+    for k in ("n_t", "n_sigma", "M", "nf", "kernel_width", "tile", "bytes_resident"):
+        assert a[k] == b[k], k
+    assert a["sigma_lo"] == pytest.approx(b["sigma_lo"], rel=1e-15)
+    assert a["sigma_hi"] == pytest.approx(b["sigma_hi"], rel=1e-15)
