@@ -30,7 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "NUFFT matvec Mpts/s (one CG iteration on K~ + eta^2 I), 2-D clustered N=1e6, Matern 3/2, eps=1e-6"
+METRIC = ("NUFFT matvec Mpts/s (one CG iteration on K~ + eta^2 I, float64-grade), 2-D clustered N=1e6, Matern 3/2, "
+          "eps=1e-6")
 UNIT = "Mpts/s"
 
 
@@ -43,8 +44,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--nu", type=float, default=1.5)
     ap.add_argument("--eps", type=float, default=1e-6)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--precision", default="df64", choices=["df64", "fp64", "fp32"],
+                    help="arithmetic of the headline path: df64 float-float (float64-grade, the default), "
+                         "fp64 native float64, fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true",
@@ -166,10 +168,15 @@ def algorithmic_bytes(info, N, R, rs):
     out = {"spread": C * R * Gocc * rs + pts + N * R * 8, "interp": C * R * Gocc * rs + pts + 2 * N * R * 8}
     if info["transform"] == 3:
         rows = C * R * (Gocc * rs + (M + 1) * ext * cp)
-        cols = 2 * C * R * (M + 1) * nf * cp
+        if info["precision"] == 2:
+            # the float-float column kernels read the rows that can be nonzero and write
+            # the rows the next stage reads: the data extent and the 2M + 1 kept modes
+            cols = C * R * (M + 1) * (ext + 2 * M + 1) * cp
+        else:
+            cols = 2 * C * R * (M + 1) * nf * cp
         box = C * R * (M + 1) * (2 * M + 1) * cp
         out.update(fft_fwd=rows + cols, fft_inv=rows + cols, diag=2 * box + pairs * (M + 1) ** 2 * rs,
-                   rows_fwd=rows, rows_inv=rows)
+                   rows_fwd=rows, rows_inv=rows, cols_fwd=cols, cols_inv=cols)
     else:
         S = nf ** (d - 1) * (nf // 2 + 1)
         nfreq = (2 * M + 1) ** (d - 1) * (M + 1)
@@ -198,15 +205,143 @@ MEASURED_TRAFFIC = {
 
 
 PHASES = ["spread", "fft_fwd", "diag", "fft_inv", "interp"]
-# one CG iteration on the 2-D path: spread, forward rows, step 3, inverse rows, interp, and
-# the CG kernels (dot partial + final, update_xr + dot final, update_p, roll, check); the
-# two column transforms are cuFFT's
-OUR_KERNELS_PER_STEP = 5 + 7
+
+
+def launches_per_step(own_columns: bool) -> int:
+    """Our kernels in one CG iteration on the 2-D path: spread, forward rows, step 3, inverse
+    rows, interp, and the CG kernels (dot partial + final, update_xr + dot final, update_p,
+    roll, check); the two column transforms are cuFFT's, or ours on float-float plans."""
+    return 5 + 7 + (2 if own_columns else 0)
+
+
+# FP32 operations of the float-float arithmetic (ff64.h): add 11 (TwoSum 6, low words 2,
+# FastTwoSum 3), mul 7 (product, three fused multiply-adds, FastTwoSum 3), complex add 22,
+# complex product 50.  In-register DFTs: DFT-2 44, DFT-4 176, DFT-8 600 (two DFT-4, the
+# W8^1 and W8^3 rotations at 36 each, eight complex adds), DFT-16 1824 (two DFT-8, four
+# general W16 rotations at 50, two W8 rotations at 36, sixteen complex adds).  A radix-16
+# Stockham pass with twiddles: DFT-16 plus 15 complex products, 2574 per 16 points.
+FF_DFT = {2: 44, 4: 176, 8: 600, 16: 1824}
+FF_PASS16 = 1824 + 15 * 50
+
+
+def ff_fft_ops(L: int) -> int:
+    """FP32 operations of one length-2^L complex FFT in the kernels' pass schedule: a first
+    pass of radix 2^(L mod 4) (or 16) at span 1 without twiddles, then radix-16 passes."""
+    r0 = 16 if L % 4 == 0 else 1 << (L % 4)
+    passes = L // 4 - (1 if L % 4 == 0 else 0)
+    nt = (1 << L) // 16
+    return nt * ((16 // r0) * FF_DFT[r0] + passes * FF_PASS16)
+
+
+def alu_ops(info, R):
+    """FP32 operations per launch of the float-float transform kernels, counted from their
+    arithmetic (the algorithm as emulated: the bound is the FP32 issue rate).
+    rows_fwd: per grid row of the data extent an nf/2-point complex FFT, then per kept mode
+      the real split (two complex adds, a complex product, two adds and two halvings: 130)
+      and the split twiddle (a complex product, shared by the RB rows of a block);
+    rows_inv: the merge of each mode pair (two merges of 116 and two twiddles of 50 per
+      pair of the nf/2 + 1 modes), then the nf/2-point FFT;
+    cols_*: one nf-point complex FFT per kept mode column."""
+    nf, M, W = info["nf"], info["M"], info["kernel_width"]
+    C = info["n_sigma"] + 1
+    L = max(info["box_hi"][a] - info["box_lo"][a] for a in range(info["d"]))
+    ext = min(nf, int(math.ceil(nf * info["dw"] * L)) + W)
+    l2 = int(round(math.log2(nf // 2)))
+    rows = C * R * ext
+    fwd = rows * (ff_fft_ops(l2) + (M + 1) * 130) + C * R * (ext // 2) * (M + 1) * 50
+    inv = rows * (ff_fft_ops(l2) + (nf // 4 + 1) * 2 * (116 + 50))
+    cols = C * R * (M + 1) * ff_fft_ops(int(round(math.log2(nf))))
+    return {"rows_fwd": fwd, "rows_inv": inv, "cols_fwd": cols, "cols_inv": cols}
+
+
+# FP32 lanes x SMs x maximum SM clock (152 x 128 x 2.07 GHz): the issue ceiling of FP32
+# instructions (a fused multiply-add is one), the peak of the float-float kernels
+FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
+
+
+def roof_of(ab, name, ms, peak, peak_src, traffic, alu_ops=None):
+    """The roofline entry of one kernel: HBM (algorithmic bytes / time against the measured
+    copy rate), or, for the float-float transform kernels, the FP32 issue rate (their
+    counted FP32 operations / time against FP32_ISSUE_PEAK), with the HBM figure beside it."""
+    ach = ab[name] / (ms * 1e-3) / 1e9
+    out = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(ach / peak, 4), "peak_source": peak_src,
+           "traffic": int(traffic) if traffic is not None else None,
+           "algorithmic_bytes": int(ab[name]), "ms_per_launch": round(ms, 4)}
+    if alu_ops:
+        ops = alu_ops / (ms * 1e-3)
+        out.update({"bound": "alu", "achieved": round(ops / 1e12, 3), "peak": round(FP32_ISSUE_PEAK / 1e12, 3),
+                    "unit": "T FP32 op/s", "frac": round(ops / FP32_ISSUE_PEAK, 4),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                    "algorithmic_ops": int(alu_ops),
+                    "hbm": {"achieved_gbs": round(ach, 1), "peak_gbs": peak, "frac": round(ach / peak, 4)}})
+    return out
+
+
+PRECISIONS = {"fp32": ("GP_FP32", "f32", 4, "f32 spread/FFT/step 3/interp, f64 CG reductions"),
+              "fp64": ("GP_FP64", "f64", 8, "f64 throughout"),
+              "df64": ("GP_DF64", "df64", 8, "float-float (two f32 words, about 48 significant bits) in spread, "
+                                           "FFT, step 3 and interp on the FP32 pipe; f64 CG reductions")}
+
+
+def _cg(abi, pl, k, yy, xx, eta2):
+    st, it, rel = abi.gp_cg_solve(pl.handle, yy, xx, 1, eta2, 1e-30, k)
+    return it[0]
+
+
+def _timed_steps(abi, torch, pl, k, yy, xx, eta2, stream):
+    """One event pair on the launching stream around exactly k CG iterations."""
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    it = _cg(abi, pl, k, yy, xx, eta2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), it
+
+
+def _step_distribution(abi, torch, pl, blocks, yy, xx, eta2, stream):
+    """Per-step milliseconds from `blocks` separate one-iteration solves, each bracketed by
+    its own events (median and p10/p90 of these)."""
+    out = []
+    for _ in range(blocks):
+        ms, it = _timed_steps(abi, torch, pl, 1, yy, xx, eta2, stream)
+        out.append(ms / max(it, 1))
+    q = np.percentile(out, [10, 50, 90])
+    return {"runs": blocks, "p10_ms": round(float(q[0]), 4), "median_ms": round(float(q[1]), 4),
+            "p90_ms": round(float(q[2]), 4),
+            "note": "each run one gp_cg_solve call of one iteration (includes its start-up: x0 = 0, r = y, "
+                    "two dot products)"}
+
+
+def _phases(abi, pl, y, x, eta2, k):
+    """Per-phase and row-kernel milliseconds from the library's own events (a separate pass)."""
+    abi.gp_profile_enable(pl.handle, True)
+    _cg(abi, pl, k, y, x, eta2)
+    phase_ms, n_rec = abi.gp_profile_read(pl.handle)
+    rows_ms = abi.gp_profile_read_rows(pl.handle)
+    abi.gp_profile_enable(pl.handle, False)
+    return phase_ms, rows_ms, n_rec
+
+
+def _kernel_ms(phase_ms, rows_ms, own_columns):
+    """Our own kernels: spread, step 3, interp, the row kernels inside the transform phases,
+    and (float-float plans) the column kernels, the rest of those phases."""
+    km = {"spread": phase_ms[0], "diag": phase_ms[2], "interp": phase_ms[4]}
+    for name, ms in zip(("rows_fwd", "rows_inv"), rows_ms):
+        if ms > 0:
+            km[name] = ms
+    if own_columns:
+        km["cols_fwd"] = phase_ms[1] - rows_ms[0]
+        km["cols_inv"] = phase_ms[3] - rows_ms[1]
+    return km
 
 
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2407_03608_gb300 as gpn
+    from paper_2407_03608_gb300 import abi
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if ws > 1:
@@ -214,7 +349,8 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     w = workload(args)
     N = w.N
-    prec = gpn.GP_FP32 if args.precision == "fp32" else gpn.GP_FP64
+    pname, dtype, rs, arith = PRECISIONS[args.precision]
+    prec = getattr(gpn, pname)
     eta2 = w.eta ** 2
     pts = torch.from_numpy(w.points).to(dev)
     s = torch.from_numpy(w.s).to(dev)
@@ -227,40 +363,22 @@ def run_ours(args, ws, rank, local):
     info = plan.info
     stream = torch.cuda.current_stream()
     x = torch.empty_like(y)
-    from paper_2407_03608_gb300 import abi
 
-    def cg_steps(pl, k, yy, xx):
-        st, it, rel = abi.gp_cg_solve(pl.handle, yy, xx, 1, eta2, 1e-30, k)
-        return it[0]
-
-    # warm-up
-    cg_steps(plan, max(args.warmup, 1), y, x)
+    # warm-up, then the timed region: K CG iterations, events on the launching stream
+    _cg(abi, plan, max(args.warmup, 1), y, x, eta2)
     torch.cuda.synchronize()
-    # timed region: K CG iterations, events on the launching stream
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    iters = cg_steps(plan, args.steps, y, x)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_total, iters = _timed_steps(abi, torch, plan, args.steps, y, x, eta2, stream)
     if ws > 1:
         dist.barrier()
-    ms_total = e0.elapsed_time(e1)
     clocks = sampler.stop()
-    # per-phase times from the library's own events, in a separate pass (the event
-    # waits it adds stay out of the timed region)
-    abi.gp_profile_enable(plan.handle, True)
-    cg_steps(plan, min(args.steps, 10), y, x)
-    phase_ms, n_rec = abi.gp_profile_read(plan.handle)
-    rows_ms = abi.gp_profile_read_rows(plan.handle)
-    abi.gp_profile_enable(plan.handle, False)
+    dist_stats = _step_distribution(abi, torch, plan, max(20, min(args.steps, 40)), y, x, eta2, stream)
+    phase_ms, rows_ms, n_rec = _phases(abi, plan, y, x, eta2, min(args.steps, 10))
     ms_total, points_job = job_totals(ms_total, N, ws, dev)
     ms_step = ms_total / iters
     value = points_job / (ms_step * 1e-3) / 1e6
@@ -278,60 +396,65 @@ def run_ours(args, ws, rank, local):
     e2e = {"value": ws * N / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
            "ms_per_step": e2e_s * 1e3}
 
-    # accuracy of this path against the plain float64 GPU path on the same K~
-    ref64 = None
+    a = torch.from_numpy(w.alpha).to(dev)
+    out_main = plan.matvec(a)
+    peak, peak_src = measured_peaks()
     extra = {}
-    if prec == gpn.GP_FP32:
-        p64 = gpn.Plan(pts, s, l, nu=w.nu, eps=w.eps, precision=gpn.GP_FP64, **plan.matched_opts())
-        a = torch.from_numpy(w.alpha).to(dev)
-        o32 = plan.matvec(a)
-        o64 = p64.matvec(a)
-        err = float(torch.linalg.norm(o32 - o64) / torch.linalg.norm(o64))
-        x64 = torch.empty_like(y)
-        cg_steps(p64, 1, y, x64)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        it64 = cg_steps(p64, args.fp64_steps, y, x64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1) / it64
-        extra["fp64_path"] = {"value": N / (ms64 * 1e-3) / 1e6, "ms_per_step": ms64, "steps": it64}
-        extra["matvec_rel_err_vs_fp64_gpu"] = err
-        ref64 = o64.cpu().numpy()
-        p64.close()
-    out_sample = plan.matvec(torch.from_numpy(w.alpha).to(dev)).cpu().numpy()
 
-    rs = 4 if prec == gpn.GP_FP32 else 8
+    def err_pair(u, v):
+        return {"rel_l2": float(torch.linalg.norm(u - v) / torch.linalg.norm(v)),
+                "rel_max": float((u - v).abs().max() / v.abs().max())}
+
+    def leg(pl, pn, own_cols):
+        """Another precision on the same K~: the same K steps, its kernels' rooflines."""
+        xx = torch.empty_like(y)
+        _cg(abi, pl, 2, y, xx, eta2)
+        ms_k, it_k = _timed_steps(abi, torch, pl, args.steps, y, xx, eta2, stream)
+        ph, rw, _ = _phases(abi, pl, y, xx, eta2, min(args.steps, 5))
+        ab_k = algorithmic_bytes(pl.info, N, 1, PRECISIONS[pn][2])
+        km = _kernel_ms(ph, rw, own_cols)
+        return {"value": round(N / (ms_k / it_k * 1e-3) / 1e6, 3), "ms_per_step": round(ms_k / it_k, 4),
+                "steps": it_k, "arith": PRECISIONS[pn][3],
+                "phase_ms": {PHASES[q]: round(ph[q], 4) for q in range(5)},
+                "roofline_kernels": [roof_of(ab_k, k, v, peak, peak_src, None) for k, v in km.items()]}
+
+    # the plain float64 GPU path on the same K~ (the comparison of the metric)
+    if prec != gpn.GP_FP64:
+        p64 = gpn.Plan(pts, s, l, nu=w.nu, eps=w.eps, precision=gpn.GP_FP64, **plan.matched_opts())
+        o64 = p64.matvec(a)
+        extra["matvec_err_vs_fp64_gpu"] = err_pair(out_main, o64)
+        extra["fp64_path"] = leg(p64, "fp64", False)
+    else:
+        o64 = out_main
+    # the mixed-precision FP32 path on the same K~
+    if prec != gpn.GP_FP32:
+        p32 = gpn.Plan(pts, s, l, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, **plan.matched_opts())
+        m32 = leg(p32, "fp32", False)
+        m32["matvec_err_vs_fp64_gpu"] = err_pair(p32.matvec(a), o64)
+        extra["mixed_fp32"] = m32
+        p32.close()
+    if prec != gpn.GP_FP64:
+        p64.close()
+    out_sample = out_main.cpu().numpy()
+
     ab = algorithmic_bytes(info, N, 1, rs)
-    # our own kernels: spread, step 3, interp, and the row kernels inside the transform
-    # phases (the rest of those phases is cuFFT's column transforms)
-    kern_ms = {"spread": phase_ms[0], "diag": phase_ms[2], "interp": phase_ms[4]}
-    for name, ms in zip(("rows_fwd", "rows_inv"), rows_ms):
-        if ms > 0:
-            kern_ms[name] = ms
+    kern_ms = _kernel_ms(phase_ms, rows_ms, prec == gpn.GP_DF64)
     dom = max(range(5), key=lambda q: phase_ms[q])
     dom_ours = max(kern_ms, key=kern_ms.get)
-    peak, peak_src = measured_peaks()
-
-    traffic = MEASURED_TRAFFIC.get((w.name, "f32" if prec == gpn.GP_FP32 else "f64", w.eps), {})
+    traffic = MEASURED_TRAFFIC.get((w.name, dtype, w.eps), {})
+    tr_ok = args.n == 1_000_000
+    alu = alu_ops(info, 1) if prec == gpn.GP_DF64 else {}
 
     def roof(name, ms):
-        ach = ab[name] / (ms * 1e-3) / 1e9
-        tr = traffic.get(name)
-        return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "peak_source": peak_src,
-                "traffic": int(tr) if tr is not None and args.n == 1_000_000 else None,
-                "algorithmic_bytes": int(ab[name]), "ms_per_launch": round(ms, 4)}
+        return roof_of(ab, name, ms, peak, peak_src, traffic.get(name) if tr_ok else None,
+                       alu_ops=alu.get(name))
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": iters,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == gpn.GP_FP32 else "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": w.name, "N": N, "d": w.d, "nu": w.nu, "eps": w.eps, "R": 1,
-                   "precision": args.precision + (" spread/FFT/step3/interp, f64 CG" if prec == gpn.GP_FP32 else ""),
+                   "precision": args.precision, "arith": arith,
                    "n_t": info["n_t"], "n_sigma": info["n_sigma"], "M": info["M"], "nf": info["nf"],
                    "kernel_width": info["kernel_width"], "tile": info["tile"], "plan_seconds": round(plan_s, 3),
                    "bytes_resident": info["bytes_resident"],
@@ -344,9 +467,10 @@ def run_ours(args, ws, rank, local):
         "dominant_phase": PHASES[dom],
         "phase_ms": {PHASES[q]: round(phase_ms[q], 4) for q in range(5)},
         "phases_recorded": n_rec,
+        "timing": dist_stats,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": OUR_KERNELS_PER_STEP * iters,
+        "gpu_launches": launches_per_step(prec == gpn.GP_DF64) * iters,
     }
     result.update(extra)
     return result, w, out_sample, plan
@@ -557,7 +681,7 @@ def run_profile_case(args):
     import paper_2407_03608_gb300 as gpn
     w = gpinputs.config_2d(args.n, 1.5) if args.d == 2 else gpinputs.config_3d(args.n)
     dev = torch.device("cuda", 0)
-    prec = gpn.GP_FP32 if args.precision == "fp32" else gpn.GP_FP64
+    prec = getattr(gpn, PRECISIONS[args.precision][0])
     plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
                     torch.from_numpy(w.l).to(dev), nu=w.nu, eps=args.eps, precision=prec,
                     transform=args.transform)

@@ -60,7 +60,13 @@ typedef enum {
   GP_EUNSUPPORTED = -8   /* a configuration the kernels do not support               */
 } gp_status;
 
-enum { GP_FP64 = 0, GP_FP32 = 1 };                 /* arithmetic of spread/FFT/step 3/interp */
+/* Arithmetic of spread/FFT/step 3/interp: float64; float32; or float-float (each value
+ * the unevaluated sum of two float32 words, about 48 significant bits, run on the FP32
+ * pipe: FP64-grade results without the FP64 pipe, whose rate on GB300 is a small
+ * fraction of the FP32 rate).  GP_DF64 is available for d = 2 with the transposed
+ * pruned transforms (transform 3, nf = 2^a <= 8192) and the stored step-3 tensor;
+ * other configurations get GP_EUNSUPPORTED. */
+enum { GP_FP64 = 0, GP_FP32 = 1, GP_DF64 = 2 };
 enum { GP_MATERN = 0, GP_SE = 1 };                 /* phi: Eq. (matern) or Eq. (squaredexp)   */
 enum { GP_PARAMS_SCALES = 0, GP_PARAMS_PAPER = 1 };/* fields are (s, l) or (w, sigma)         */
 

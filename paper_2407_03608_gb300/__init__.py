@@ -16,7 +16,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import abi
-from .abi import (GP_FP32, GP_FP64, GP_MATERN, GP_PARAMS_PAPER, GP_PARAMS_SCALES, GP_SE, GPError,  # noqa: F401
+from .abi import (GP_DF64, GP_FP32, GP_FP64, GP_MATERN, GP_PARAMS_PAPER, GP_PARAMS_SCALES, GP_SE, GPError,  # noqa: F401
                   gp_cg_solve, gp_cg_solve_refined, gp_destroy, gp_matvec, gp_plan, gp_profile_enable, gp_profile_read,
                   gp_profile_read_rows,
                   gp_plan_info_get, gp_posterior_mean, gp_posterior_variance, gp_version)
@@ -24,7 +24,7 @@ from .abi import (GP_FP32, GP_FP64, GP_MATERN, GP_PARAMS_PAPER, GP_PARAMS_SCALES
 __all__ = ["Plan", "GPError", "gp_plan", "gp_matvec", "gp_cg_solve", "gp_cg_solve_refined", "gp_posterior_mean",
            "gp_posterior_variance",
            "gp_profile_enable", "gp_profile_read", "gp_profile_read_rows",
-           "gp_plan_info_get", "gp_destroy", "gp_version", "GP_FP32", "GP_FP64", "GP_MATERN", "GP_SE",
+           "gp_plan_info_get", "gp_destroy", "gp_version", "GP_FP32", "GP_FP64", "GP_DF64", "GP_MATERN", "GP_SE",
            "GP_PARAMS_SCALES", "GP_PARAMS_PAPER"]
 
 

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgpnufft.so")
 
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ECUFFT, GP_ENOTCONV, GP_EBREAKDOWN, GP_ETIMEOUT, GP_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
-GP_FP64, GP_FP32 = 0, 1
+GP_FP64, GP_FP32, GP_DF64 = 0, 1, 2
 GP_NOALLOC_MAX_QUERIES = 32768
 GP_MATERN, GP_SE = 0, 1
 GP_PARAMS_SCALES, GP_PARAMS_PAPER = 0, 1

@@ -369,8 +369,11 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   for (int q = 0; q < d - 1; ++q) nfreq *= (2 * h.M + 1);
   nfreq *= (h.M + 1);
   GPN_CHECK(o.transform >= 0 && o.transform <= 3, GP_EINVAL, "transform must be 0, 1, 2 or 3");
-  const bool row_ok = rowfft_supported(d, h.nf, rs);
-  const bool t3_ok = tr3_supported(d, h.nf, rs);
+  const bool ddp = o.precision == GP_DF64;
+  const bool row_ok = !ddp && rowfft_supported(d, h.nf, rs);
+  const bool t3_ok = tr3_supported(d, h.nf, o.precision);
+  GPN_CHECK(!ddp || (d == 2 && t3_ok && (o.transform == 0 || o.transform == 3)), GP_EUNSUPPORTED,
+            "GP_DF64 needs d = 2 with the transposed pruned transforms (transform 3, nf = 2^a <= 8192)");
   GPN_CHECK(o.transform != 2 || row_ok, GP_EUNSUPPORTED, "pruned row transforms need d <= 2 and power-of-two nf");
   GPN_CHECK(o.transform != 3 || t3_ok, GP_EUNSUPPORTED, "transposed pruned transforms need d = 2 and nf = 2^a");
   // auto: the transposed pruned transforms for d = 2; the pruned row transforms for
@@ -396,7 +399,10 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   GPN_CHECK(o.step3 >= 0 && o.step3 <= 2, GP_EINVAL, "step3 must be 0, 1 or 2");
   GPN_CHECK(o.step3 != 2 || !ps.rowfft, GP_EUNSUPPORTED,
             "the memory-lean step 3 runs with transform 1 or 3, not the pruned row transforms");
-  if (o.step3 == 2) {
+  GPN_CHECK(o.step3 != 2 || !ddp, GP_EUNSUPPORTED, "GP_DF64 plans use the stored step-3 tensor (step3 = 1)");
+  if (ddp) {
+    ps.lean = false;
+  } else if (o.step3 == 2) {
     ps.lean = true;
   } else if (o.step3 == 0 && !ps.rowfft) {
     const long long with_a = ps.est_rest + ps.a_bytes, with_f = ps.est_rest + ps.lean_bytes;
@@ -418,7 +424,8 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   GPN_CHECK(o.family == GP_MATERN || o.family == GP_SE, GP_EINVAL, "family must be GP_MATERN or GP_SE");
   GPN_CHECK(o.family == GP_SE || (nu > 0.0 && std::isfinite(nu)), GP_EINVAL, "nu must be > 0");
   GPN_CHECK(eps > 0.0 && eps <= 0.1, GP_EINVAL, "eps must be in (0, 0.1]");
-  GPN_CHECK(o.precision == GP_FP64 || o.precision == GP_FP32, GP_EINVAL, "precision must be GP_FP64 or GP_FP32");
+  GPN_CHECK(o.precision == GP_FP64 || o.precision == GP_FP32 || o.precision == GP_DF64, GP_EINVAL,
+            "precision must be GP_FP64, GP_FP32 or GP_DF64");
   GPN_CHECK(o.param_mode == GP_PARAMS_SCALES || o.param_mode == GP_PARAMS_PAPER, GP_EINVAL, "bad param_mode");
   int max_rhs = o.max_rhs > 0 ? o.max_rhs : 1;
   GPN_CHECK(max_rhs <= 1024, GP_EINVAL, "max_rhs must be <= 1024");
@@ -476,6 +483,8 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   if (o.diag_correct) build_diag_correction(*plan, w, sig, st);
   build_active_tiles(*plan, bstart);
   if (spread2d_supported(*plan)) build_spread2d_tiles(*plan, bstart);
+  GPN_CHECK(o.precision != GP_DF64 || plan->sp2_tiles, GP_EUNSUPPORTED,
+            "GP_DF64 needs the two-dimensional register spread (kernel width <= 16, channels <= 32)");
   if (plan->lean) {
     build_lean_tables(*plan);
     GPN_CHECK(lean_smem_bytes(*plan) <= (size_t(200) << 10), GP_EUNSUPPORTED,
@@ -525,7 +534,7 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->partials = (double*)plan->alloc(sizeof(double) * 512 * max_rhs);
   GPN_CUDA(cudaMallocHost(&plan->host_scal, sizeof(double) * 8 * max_rhs));
   if (plan->tr3) {
-    plan->t3_plan(1);
+    if (o.precision != GP_DF64) plan->t3_plan(1);   // float-float columns are the library's own kernel
   } else if (plan->rowfft) {
     if (d == 2) plan->col_plan(1);
   } else {
@@ -663,7 +672,7 @@ int gp_tile_candidates(int d, int n_channels, int precision, int width, int* til
   return guarded([&]() {
     GPN_CHECK(d >= 1 && d <= 3 && n_channels >= 1 && n_channels <= kMaxChannels && width >= 2 && width <= kMaxWidth,
               GP_EINVAL, "bad d, n_channels or width");
-    GPN_CHECK(precision == GP_FP64 || precision == GP_FP32, GP_EINVAL, "bad precision");
+    GPN_CHECK(precision == GP_FP64 || precision == GP_FP32 || precision == GP_DF64, GP_EINVAL, "bad precision");
     GPN_CHECK(tiles != nullptr || max_tiles == 0, GP_EINVAL, "null output");
     const auto c = tile_candidates(d, n_channels, precision == GP_FP32 ? 4 : 8, width);
     const int n = std::min<int>((int)c.size(), max_tiles);
@@ -934,7 +943,8 @@ int gp_plan_params(int d, long long N, double nu, double eps, double scale_min, 
     GPN_CHECK(o.family == GP_MATERN || o.family == GP_SE, GP_EINVAL, "family must be GP_MATERN or GP_SE");
     GPN_CHECK(o.family == GP_SE || (nu > 0.0 && std::isfinite(nu)), GP_EINVAL, "nu must be > 0");
     GPN_CHECK(eps > 0.0 && eps <= 0.1, GP_EINVAL, "eps must be in (0, 0.1]");
-    GPN_CHECK(o.precision == GP_FP64 || o.precision == GP_FP32, GP_EINVAL, "precision must be GP_FP64 or GP_FP32");
+    GPN_CHECK(o.precision == GP_FP64 || o.precision == GP_FP32 || o.precision == GP_DF64, GP_EINVAL,
+              "precision must be GP_FP64, GP_FP32 or GP_DF64");
     const PlanShape ps = plan_shape(d, N, nu, eps, o, sigma_min, sigma_max, box_lo, box_hi, -1, nullptr);
     std::memset(info, 0, sizeof(*info));
     fill_hyper_info(ps.h, info);

@@ -47,6 +47,10 @@ template <>
 struct Vec2<double> {
   using type = double2;
 };
+template <>
+struct Vec2<dd> {
+  using type = cpx<dd>;
+};
 
 // RB adjacent complex values to global memory (16-byte stores where possible)
 template <typename T, int RB>
@@ -89,7 +93,7 @@ __host__ __device__ constexpr int tw_hi(int n2) { return n2 / 64 + 1; }
 // two-level tables (measured: the inverse kernel runs faster with the smaller
 // shared-memory footprint).
 template <typename T, bool INV>
-__host__ __device__ constexpr bool pass_tables_in_smem() { return sizeof(T) == 4 && !INV; }
+__host__ __device__ constexpr bool pass_tables_in_smem() { return (sizeof(T) == 4 && !INV) || is_dd<T>::value; }
 // twiddle entries staged by a row kernel: the two-level tables of the length-N2 FFT
 // ([hi][lo]) and of the real split ([hi][lo]), then (FP32) the pass tables; padded to
 // whole 16-byte chunks
@@ -353,6 +357,140 @@ __global__ void __launch_bounds__(RB*(1 << L) / 16, (rows_min_blocks<T, L, RB>()
   if (first) cp_async_wait_all();
 }
 
+// ---- column transforms (float-float plans) -------------------------------------------
+//
+// The first-axis transforms of the transposed layout: every (rhs, channel, mode m)
+// column of nf complex values is contiguous, so one CTA takes one column, loads it
+// into registers (16 values a thread, coalesced), runs the Stockham passes through
+// shared memory and writes the last pass straight back.  Rows known to be zero are
+// not read, and only the rows the next stage reads are written:
+//   forward (X -> Y): input rows [row_lo, row_hi) (the data extent; the row stage
+//     writes no others), output rows |n_1| <= M (what step 3 reads);
+//   inverse (Z -> Y): input rows |n_1| <= M (step 3 writes no others), output rows
+//     [out_lo, out_hi) (the row groups the inverse row kernel reads).
+// Twiddles come from the pass tables of the length-nf FFT in global memory (L1/L2
+// resident; too large for shared memory next to a 16-byte-per-value column).
+
+// one complex value through the read-only path
+template <typename T>
+__device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ cpx<dd> ldg_c<dd>(const cpx<dd>* p) {
+  const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+  return {dd(u.x, u.y), dd(u.z, u.w)};
+}
+
+// twiddles of one radix-16 pass from a pass table in global memory ([r - 1][k])
+template <typename T>
+struct GPassTwiddle {
+  const cpx<T>* tab;
+  int Ns;
+  __device__ __forceinline__ cpx<T> operator()(int r, int k, int) const { return ldg_c(tab + (r - 1) * Ns + k); }
+};
+
+// In-place complex FFT of length N = 2^L (L >= 5) with NT = N / 16 threads: the first
+// pass (radix 2^(L mod 4), or 16) from the registers x[u] = element t + u NT, the
+// middle passes through the buffer, and the last pass (radix 16 at span N/16) handed to
+// out(r, v), output r of thread t being element t + r NT.  No barrier follows.
+template <bool INV, int L, typename T, typename Out>
+__device__ __forceinline__ void fft_block_regs_to(cpx<T>* b, const cpx<T> (&x)[16], const cpx<T>* ptab, int t,
+                                                  Out out) {
+  constexpr int N = 1 << L, NT = N / 16;
+  constexpr int R0 = (L % 4 == 0) ? 16 : (1 << (L % 4));
+  constexpr int S = (L % 4 == 0) ? L / 4 - 1 : L / 4;   // radix-16 passes after the first
+  static_assert(L >= 5, "at least one radix-16 pass after the first");
+  {
+    fft::Pass<R0, 16 / R0, T> p;
+    fft::first_pass_inputs(p, x);
+    p.template compute<INV>(GPassTwiddle<T>{ptab, 1}, N, 1, t, NT);   // span 1: no twiddles
+    p.write(b, 1, t, NT);
+  }
+  __syncthreads();
+  int Ns = R0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    fft::Pass<16, 1, T> p;
+    p.load(b, N, t, NT);
+    __syncthreads();
+    p.template compute<INV>(GPassTwiddle<T>{ptab + fft::pass_table_offset(L, Ns), Ns}, N, Ns, t, NT);
+    if (s + 1 < S) {
+      p.write(b, Ns, t, NT);
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) out(r, p.v[0][r]);
+    }
+    Ns *= 16;
+  }
+}
+
+template <typename T>
+struct ColsArgs {
+  const cpx<T>* in;        // [col][nf]
+  cpx<T>* out;             // [col][nf]
+  const cpx<T>* ptab;      // pass tables of the length-nf FFT
+  long long ncols;         // C R (M + 1)
+  int in_lo0, in_hi0, in_lo1, in_hi1;     // input rows that may be nonzero: two ranges
+  int out_lo0, out_hi0, out_lo1, out_hi1; // output rows written: two ranges
+};
+
+__device__ __forceinline__ bool in_ranges(int y, int a0, int a1, int b0, int b1) {
+  return (y >= a0 && y < a1) || (y >= b0 && y < b1);
+}
+
+template <typename T, int L, bool INV>
+__global__ void __launch_bounds__((1 << L) / 16, 1) k_cols(ColsArgs<T> a) {
+  constexpr int N = 1 << L, NT = N / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* b = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int t = threadIdx.x;
+  for (long long col = blockIdx.x; col < a.ncols; col += gridDim.x) {
+    const cpx<T>* src = a.in + (size_t)col * N;
+    cpx<T>* dst = a.out + (size_t)col * N;
+    cpx<T> v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int y = t + u * NT;
+      v[u] = in_ranges(y, a.in_lo0, a.in_hi0, a.in_lo1, a.in_hi1) ? ldg_c(src + y) : cpx<T>{T(0), T(0)};
+    }
+    __syncthreads();   // the previous column's last pass has read the buffer
+    fft_block_regs_to<INV, L>(b, v, a.ptab, t, [&](int r, const cpx<T>& val) {
+      const int y = t + r * NT;
+      if (in_ranges(y, a.out_lo0, a.out_hi0, a.out_lo1, a.out_hi1)) dst[y] = val;
+    });
+  }
+}
+
+template <typename T>
+constexpr size_t cols_smem(int L) {
+  return (size_t)((1 << L) + (1 << L) / 16) * sizeof(cpx<T>);
+}
+
+template <typename T, int L>
+void cols_launch(bool inv, const ColsArgs<T>& a, cudaStream_t st) {
+  const size_t smem = cols_smem<T>(L);
+  void (*k)(ColsArgs<T>) = inv ? k_cols<T, L, true> : k_cols<T, L, false>;
+  GPN_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k<<<(unsigned)a.ncols, (1 << L) / 16, smem, st>>>(a);
+}
+
+template <typename T>
+void cols(bool inv, int L, const ColsArgs<T>& a, cudaStream_t st) {
+  switch (L) {
+    case 5: cols_launch<T, 5>(inv, a, st); break;
+    case 6: cols_launch<T, 6>(inv, a, st); break;
+    case 7: cols_launch<T, 7>(inv, a, st); break;
+    case 8: cols_launch<T, 8>(inv, a, st); break;
+    case 9: cols_launch<T, 9>(inv, a, st); break;
+    case 10: cols_launch<T, 10>(inv, a, st); break;
+    case 11: cols_launch<T, 11>(inv, a, st); break;
+    case 12: cols_launch<T, 12>(inv, a, st); break;
+    default: cols_launch<T, 13>(inv, a, st);
+  }
+}
+
 template <typename T>
 struct DiagTArgs {
   const cpx<T>* Y;         // column transforms [cr][M+1][nf]
@@ -388,7 +526,7 @@ __global__ void __launch_bounds__(128) k_diag_t(DiagTArgs<T> a) {
   if constexpr (kReg && NC <= 11) {
     T av[NP];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) av[p] = __ldg(Am + (size_t)p * pstride);
+    for (int p = 0; p < NP; ++p) av[p] = ldg_val(Am + (size_t)p * pstride);
     for (int r = 0; r < a.R; ++r) {
       const cpx<T>* Yr = a.Y + (size_t)r * NC * colstride;
       cpx<T>* Zr = a.Z + (size_t)r * NC * colstride;
@@ -405,10 +543,10 @@ __global__ void __launch_bounds__(128) k_diag_t(DiagTArgs<T> a) {
         for (int l = 0; l < NC; ++l) {
           const int lo = k < l ? k : l, hi = k < l ? l : k;
           const T w = av[lo * NC - lo * (lo - 1) / 2 + (hi - lo)];
-          ap.x += w * bp[l].x;
-          ap.y += w * bp[l].y;
-          an.x += w * bn[l].x;
-          an.y += w * bn[l].y;
+          madd(ap.x, w, bp[l].x);
+          madd(ap.y, w, bp[l].y);
+          madd(an.x, w, bn[l].x);
+          madd(an.y, w, bn[l].y);
         }
         Zr[k * colstride + off_p] = ap;
         if (n1 != 0) Zr[k * colstride + off_n] = an;
@@ -443,10 +581,10 @@ __global__ void __launch_bounds__(128) k_diag_t(DiagTArgs<T> a) {
           xp = Yr[l * colstride + off_p];
           xn = Yr[l * colstride + off_n];
         }
-        ap.x += w * xp.x;
-        ap.y += w * xp.y;
-        an.x += w * xn.x;
-        an.y += w * xn.y;
+        madd(ap.x, w, xp.x);
+        madd(ap.y, w, xp.y);
+        madd(an.x, w, xn.x);
+        madd(an.y, w, xn.y);
       }
       Zr[k * colstride + off_p] = ap;
       if (n1 != 0) Zr[k * colstride + off_n] = an;
@@ -471,6 +609,11 @@ void diag_dispatch(const DiagTArgs<T>& a, cudaStream_t st) {
 
 constexpr int kMinLog = 4, kMaxLog = 13;       // nf = 32 .. 16384
 constexpr size_t kRowSmemMax = size_t(150) << 10;
+// float-float row kernels also stage their pass tables (one 16-byte load a twiddle
+// instead of a float-float complex product)
+constexpr size_t kRowSmemMaxDD = size_t(215) << 10;
+template <typename T>
+constexpr size_t row_smem_max() { return is_dd<T>::value ? kRowSmemMaxDD : kRowSmemMax; }
 
 template <typename T, int L, int RB>
 void rows_launch(bool inv, const RowsArgs<T>& a, cudaStream_t st) {
@@ -489,7 +632,7 @@ void rows_launch(bool inv, const RowsArgs<T>& a, cudaStream_t st) {
 // test as rows_per_block)
 template <typename T, int L, int RB>
 constexpr bool rows_fit() {
-  return std::max(row_smem<T, false>(L, RB), row_smem<T, true>(L, RB)) <= kRowSmemMax &&
+  return std::max(row_smem<T, false>(L, RB), row_smem<T, true>(L, RB)) <= row_smem_max<T>() &&
          RB * (1 << L) / 16 <= 1024;
 }
 
@@ -558,18 +701,23 @@ void rows_run(Plan& plan, bool inv, const void* X, int R, cudaStream_t st) {
 
 }  // namespace
 
-bool tr3_supported(int d, long long nf, size_t rs) {
+bool tr3_supported(int d, long long nf, int precision) {
   if (d != 2) return false;
   const int L = log2_exact(nf / 2);
   if (nf % 2 || L < kMinLog || L > kMaxLog) return false;
-  return (rs == 4 ? row_smem<float, false>(L, 1) : row_smem<double, false>(L, 1)) <= kRowSmemMax;
+  if (precision == GP_DF64)   // the float-float column kernel holds a column of nf values
+    return L + 1 >= 5 && L + 1 <= 13 && row_smem<dd, false>(L, 1) <= kRowSmemMaxDD &&
+           cols_smem<dd>(L + 1) <= kRowSmemMaxDD;
+  return (precision == GP_FP32 ? row_smem<float, false>(L, 1) : row_smem<double, false>(L, 1)) <= kRowSmemMax;
 }
 
 void tr3_setup(Plan& plan) {
   const long long nf = plan.geom.nf, N2 = nf / 2;
   const int L = log2_exact(N2);
-  const size_t sm2 = plan.precision == GP_FP32 ? row_smem<float, false>(L, 2) : row_smem<double, false>(L, 2);
-  plan.t3_rb = (sm2 <= kRowSmemMax && 2 * (N2 / 16) <= 1024) ? 2 : 1;
+  const bool f32 = plan.precision == GP_FP32, ddp = plan.precision == GP_DF64;
+  const size_t sm2 = f32 ? row_smem<float, false>(L, 2) : (ddp ? row_smem<dd, false>(L, 2) : row_smem<double, false>(L, 2));
+  const size_t smax = ddp ? kRowSmemMaxDD : kRowSmemMax;
+  plan.t3_rb = (sm2 <= smax && 2 * (N2 / 16) <= 1024) ? 2 : 1;
   // two-level tables, computed in float64: W_{N2}^{64 q} (q < H), W_{N2}^j (j < 64),
   // W_nf^{64 q} (q < H), W_nf^j (j < 64), with H = N2 / 64 + 1
   const int H = tw_hi((int)N2);
@@ -584,20 +732,56 @@ void tr3_setup(Plan& plan) {
   for (int j = 0; j < 64; ++j) put(j, N2);
   for (int q = 0; q < H; ++q) put(64ll * q, nf);
   for (int j = 0; j < 64; ++j) put(j, nf);
-  if (plan.precision == GP_FP32) {
+  if (f32 || ddp) {
     const std::vector<double> pt = fft::pass_tables(L);
     w.insert(w.end(), pt.begin(), pt.end());
   }
-  const size_t count = plan.precision == GP_FP32 ? tw_count<float, false>(L) : tw_count<double, false>(L);
+  const size_t count = f32 ? tw_count<float, false>(L) : (ddp ? tw_count<dd, false>(L) : tw_count<double, false>(L));
   w.resize(2 * count, 0.0);  // padded to whole 16-byte chunks
   plan.tw_half = plan.alloc(w.size() * plan.real_size);
-  if (plan.precision == GP_FP32) {
+  auto upload_dd = [&](void* dst, const std::vector<double>& v) {
+    std::vector<dd> f(v.size());
+    for (size_t i = 0; i < v.size(); ++i) f[i] = dd(v[i]);
+    GPN_CUDA(cudaMemcpy(dst, f.data(), f.size() * sizeof(dd), cudaMemcpyHostToDevice));
+  };
+  if (f32) {
     std::vector<float> f(w.begin(), w.end());
     GPN_CUDA(cudaMemcpy(plan.tw_half, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+  } else if (ddp) {
+    upload_dd(plan.tw_half, w);
+    // the column transforms' pass tables (length nf), read from global memory
+    const std::vector<double> ct = fft::pass_tables(L + 1);
+    plan.col_tw = plan.alloc(std::max<size_t>(ct.size(), 2) * sizeof(dd));
+    if (!ct.empty()) upload_dd(plan.col_tw, ct);
   } else {
     GPN_CUDA(cudaMemcpy(plan.tw_half, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
 }
+
+namespace {
+// the column transforms of the float-float plans (cuFFT has no float-float type)
+void cols_run_dd(Plan& plan, bool inv, const void* in, void* out, int R, cudaStream_t st) {
+  ColsArgs<dd> a{};
+  a.in = (const cpx<dd>*)in;
+  a.out = (cpx<dd>*)out;
+  a.ptab = (const cpx<dd>*)plan.col_tw;
+  a.ncols = (long long)plan.geom.C * R * (plan.geom.M + 1);
+  const int nf = (int)plan.geom.nf, M = (int)plan.geom.M;
+  // the row groups of the inverse row kernel: [row0, row0 + npairs RB)
+  const int row0 = plan.row_lo / plan.t3_rb * plan.t3_rb;
+  const int rows_end = std::min(nf, row0 + (plan.row_hi - row0 + plan.t3_rb - 1) / plan.t3_rb * plan.t3_rb);
+  if (!inv) {
+    a.in_lo0 = plan.row_lo, a.in_hi0 = plan.row_hi, a.in_lo1 = 0, a.in_hi1 = 0;
+    a.out_lo0 = 0, a.out_hi0 = M + 1, a.out_lo1 = nf - M, a.out_hi1 = nf;
+  } else {
+    a.in_lo0 = 0, a.in_hi0 = M + 1, a.in_lo1 = nf - M, a.in_hi1 = nf;
+    a.out_lo0 = row0, a.out_hi0 = rows_end, a.out_lo1 = 0, a.out_hi1 = 0;
+  }
+  if (a.ncols == 0) return;
+  cols<dd>(inv, log2_exact(nf), a, st);
+  GPN_CUDA(cudaGetLastError());
+}
+}  // namespace
 
 cufftHandle Plan::t3_plan(int R) {
   auto it = fft_t3.find(R);
@@ -611,6 +795,12 @@ cufftHandle Plan::t3_plan(int R) {
 }
 
 void tr3_forward(Plan& plan, int R, cudaStream_t st) {
+  if (plan.precision == GP_DF64) {
+    rows_run<dd>(plan, false, plan.fx, R, st);
+    prof_mark(plan, 0, st);
+    cols_run_dd(plan, false, plan.fx, plan.fy, R, st);
+    return;
+  }
   cufftHandle h = plan.t3_plan(R);
   if (plan.precision == GP_FP32) {
     rows_run<float>(plan, false, plan.fx, R, st);
@@ -626,7 +816,11 @@ void tr3_forward(Plan& plan, int R, cudaStream_t st) {
 }
 
 void tr3_diag(Plan& plan, int R, cudaStream_t st) {
-  if (plan.precision == GP_FP32) {
+  if (plan.precision == GP_DF64) {
+    DiagTArgs<dd> a{(const cpx<dd>*)plan.fy, (cpx<dd>*)plan.fz, (const dd*)plan.a_tensor, plan.geom.nf,
+                    (int)plan.geom.M, plan.geom.C, R};
+    diag_dispatch<dd, 1>(a, st);
+  } else if (plan.precision == GP_FP32) {
     DiagTArgs<float> a{(const cpx<float>*)plan.fy, (cpx<float>*)plan.fz, (const float*)plan.a_tensor,
                        plan.geom.nf, (int)plan.geom.M, plan.geom.C, R};
     diag_dispatch<float, 1>(a, st);
@@ -639,6 +833,12 @@ void tr3_diag(Plan& plan, int R, cudaStream_t st) {
 }
 
 void tr3_inverse(Plan& plan, int R, cudaStream_t st) {
+  if (plan.precision == GP_DF64) {
+    cols_run_dd(plan, true, plan.fz, plan.fy, R, st);
+    prof_mark(plan, 1, st);
+    rows_run<dd>(plan, true, plan.fy, R, st);
+    return;
+  }
   cufftHandle h = plan.t3_plan(R);
   GPN_CUFFT3(cufftSetStream(h, st));
   if (plan.precision == GP_FP32) {

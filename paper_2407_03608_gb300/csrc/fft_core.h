@@ -10,6 +10,8 @@
 #include <cmath>
 #include <vector>
 
+#include "ff64.h"
+
 namespace gpn {
 namespace fft {
 
@@ -24,6 +26,11 @@ namespace fft {
 template <typename T>
 struct cpx {
   T x, y;
+};
+// a float-float complex value is 16 bytes: aligned so that it moves in one vector access
+template <>
+struct alignas(16) cpx<dd> {
+  dd x, y;
 };
 
 template <typename T>

@@ -194,10 +194,10 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
         if (active) {
           const T* rowp = st + l0[0];
           for (int i = 0; i < W; ++i) {
-            const T wgt = es_psi<T>((T)i - x[0], a.beta, a.inv_halfw);
+            const T wgt = psi_at<T>(i, x[0], a.beta, a.inv_halfw);
 #pragma unroll
             for (int k = 0; k < CMAX; ++k)
-              if (EXACT || k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+              if (EXACT || k < ncur) madd(acc[k], wgt, rowp[(size_t)k * SV + i]);
           }
         }
       } else {
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
         const int src = kGroup == 0 ? grp * Gs : 0;
         T pq[kMaxDim];
 #pragma unroll
-        for (int q = 0; q < D; ++q) pq[q] = gl < W ? es_psi<T>((T)gl - x[q], a.beta, a.inv_halfw) : T(0);
+        for (int q = 0; q < D; ++q) pq[q] = gl < W ? psi_at<T>(gl, x[q], a.beta, a.inv_halfw) : T(0);
         for (int pen0 = 0; pen0 < P; pen0 += Gs) {
           const int pen = pen0 + gl;
           const bool valid = active && pen < P;
@@ -220,17 +220,17 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
           }
 #pragma unroll
           for (int q = 0; q < D - 1; ++q) {
-            plead *= __shfl_sync(0xffffffffu, pq[q], src + iq[q]);
+            plead *= shfl_val(pq[q], src + iq[q]);
             off = off * E + l0[q] + iq[q];
           }
           const T* rowp = st + (size_t)off * EP + l0[D - 1];
 #pragma unroll 3
           for (int i = 0; i < W; ++i) {
-            const T wgt = plead * __shfl_sync(0xffffffffu, pq[D - 1], src + i);
+            const T wgt = plead * shfl_val(pq[D - 1], src + i);
             if (valid) {
 #pragma unroll
               for (int k = 0; k < CMAX; ++k)
-                if (EXACT || k < ncur) acc[k] += wgt * rowp[(size_t)k * SV + i];
+                if (EXACT || k < ncur) madd(acc[k], wgt, rowp[(size_t)k * SV + i]);
             }
           }
         }
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
         for (int k = 0; k < CMAX; ++k) {
           if (k < ncur) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            for (int o = 16; o > 0; o >>= 1) acc[k] += shfl_xor_val(acc[k], o);
           }
         }
       } else if (kGroup == 0) {
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
         for (int k = 0; k < CMAX; ++k) {
           if (k < ncur) {
             for (int o = 1; o < Gs; o <<= 1) {
-              const T v = __shfl_down_sync(0xffffffffu, acc[k], o);
+              const T v = shfl_down_val(acc[k], o);
               if (gl + o < Gs) acc[k] += v;
             }
           }
@@ -398,6 +398,8 @@ void launch_interp(Plan& plan, const PointSet& ps, const double* alpha_sorted, d
   if (ps.n == 0) return;
   if (plan.precision == GP_FP32)
     interp_impl<float>(plan, ps, alpha_sorted, shift, out_sorted, R, st);
+  else if (plan.precision == GP_DF64)
+    interp_impl<dd>(plan, ps, alpha_sorted, shift, out_sorted, R, st);
   else
     interp_impl<double>(plan, ps, alpha_sorted, shift, out_sorted, R, st);
 }

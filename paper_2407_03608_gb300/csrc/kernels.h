@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "ff64.h"
 #include "plan.h"
 
 namespace gpn {
@@ -16,6 +17,16 @@ struct Cplx<float> {
 template <>
 struct Cplx<double> {
   using type = double2;
+};
+
+// Storage type of a plan precision: GP_FP32 float, GP_FP64 double, GP_DF64 dd (float-float).
+template <typename T>
+struct is_dd {
+  static constexpr bool value = false;
+};
+template <>
+struct is_dd<dd> {
+  static constexpr bool value = true;
 };
 
 // Exponential-of-semicircle spreading kernel psi(s) = exp(beta (sqrt(1 - (2s/w)^2) - 1))
@@ -43,6 +54,73 @@ __device__ __forceinline__ double es_psi<double>(double s, double beta, double i
 template <typename T>
 inline T es_beta_arg(double beta) {
   return sizeof(T) == 4 ? (T)(beta * 1.4426950408889634074) : (T)beta;
+}
+
+// psi(j - xi) at the integer cell offset j.  Float-float plans evaluate the kernel in
+// float64 (exp and sqrt to double precision) and round it to float-float: the offset
+// xi is exact in both words, and the kernel values then carry about 1e-16 relative
+// error, far below the float-float rounding of the sums they enter.
+template <typename T>
+__device__ __forceinline__ T psi_at(int j, T xi, T beta, T inv_halfw) {
+  return es_psi<T>((T)j - xi, beta, inv_halfw);
+}
+template <>
+__device__ __forceinline__ dd psi_at<dd>(int j, dd xi, dd beta, dd inv_halfw) {
+  const double s = ((double)j - (double)xi.hi) - (double)xi.lo;
+  return dd(es_psi<double>(s, (double)beta, (double)inv_halfw));
+}
+
+// Warp shuffles of plan values (a float-float value moves as its two words).
+template <typename T>
+__device__ __forceinline__ T shfl_val(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+template <>
+__device__ __forceinline__ dd shfl_val<dd>(dd v, int src) {
+  return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+template <typename T>
+__device__ __forceinline__ T shfl_down_val(T v, int o) {
+  return __shfl_down_sync(0xffffffffu, v, o);
+}
+template <>
+__device__ __forceinline__ dd shfl_down_val<dd>(dd v, int o) {
+  return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+template <typename T>
+__device__ __forceinline__ T shfl_xor_val(T v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+template <>
+__device__ __forceinline__ dd shfl_xor_val<dd>(dd v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// acc += a b (one fused step for float-float)
+template <typename T>
+__device__ __forceinline__ void madd(T& acc, T a, T b) {
+  acc += a * b;
+}
+template <>
+__device__ __forceinline__ void madd<dd>(dd& acc, dd a, dd b) {
+  acc = fma_dd(a, b, acc);
+}
+
+// Read-only load of a plan value
+template <typename T>
+__device__ __forceinline__ T ldg_val(const T* p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ dd ldg_val<dd>(const dd* p) {
+  const float2 u = __ldg(reinterpret_cast<const float2*>(p));
+  return {u.x, u.y};
+}
+
+// A plan value to float64
+template <typename T>
+__device__ __forceinline__ double to_f64(T v) {
+  return (double)v;
 }
 
 // Channel-count buckets: kernels keep per-channel values in registers sized by a

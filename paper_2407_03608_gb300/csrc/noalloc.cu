@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_query_interp(QueryArgs<T> a) {
     // lane j < W holds psi(j - xi_q) for every axis q
     T pq[D];
 #pragma unroll
-    for (int q = 0; q < D; ++q) pq[q] = lane < W ? es_psi<T>((T)lane - xi[q], a.beta, a.inv_halfw) : T(0);
+    for (int q = 0; q < D; ++q) pq[q] = lane < W ? psi_at<T>(lane, xi[q], a.beta, a.inv_halfw) : T(0);
     T acc[CMAX];
 #pragma unroll
     for (int k = 0; k < CMAX; ++k) acc[k] = T(0);
@@ -148,21 +148,21 @@ __global__ void __launch_bounds__(256) k_query_interp(QueryArgs<T> a) {
       long long off = 0;
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        wgt *= __shfl_sync(0xffffffffu, pq[q], iq[q]);
+        wgt *= shfl_val(pq[q], iq[q]);
         off = off * a.nf + l0[q] + iq[q];
       }
       if (valid) {
         const T* gp = a.grid + off;
 #pragma unroll
         for (int k = 0; k < CMAX; ++k)
-          if (k < a.C) acc[k] += wgt * __ldg(gp + (size_t)k * a.G);
+          if (k < a.C) madd(acc[k], wgt, ldg_val(gp + (size_t)k * a.G));
       }
     }
 #pragma unroll
     for (int k = 0; k < CMAX; ++k) {
       if (k < a.C) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        for (int o = 16; o > 0; o >>= 1) acc[k] += shfl_xor_val(acc[k], o);
       }
     }
     if (lane == 0) {
@@ -270,6 +270,8 @@ void launch_query_interp(Plan& plan, const double* x, const double* fa, const do
   if (nq == 0) return;
   if (plan.precision == GP_FP32)
     query_impl<float>(plan, x, fa, fb, nq, mu, bad, sms, st);
+  else if (plan.precision == GP_DF64)
+    query_impl<dd>(plan, x, fa, fb, nq, mu, bad, sms, st);
   else
     query_impl<double>(plan, x, fa, fb, nq, mu, bad, sms, st);
 }

@@ -11,6 +11,7 @@
 
 #include <cmath>
 
+#include "ff64.h"
 #include "plan.h"
 
 namespace gpn {
@@ -69,6 +70,7 @@ __device__ void build_a_body(const ATensorArgs<T>& a) {
 
 __global__ void k_build_a_f32(ATensorArgs<float> a) { build_a_body<float>(a); }
 __global__ void k_build_a_f64(ATensorArgs<double> a) { build_a_body<double>(a); }
+__global__ void k_build_a_dd(ATensorArgs<dd> a) { build_a_body<dd>(a); }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
@@ -89,6 +91,9 @@ void build_a_tensor(Plan& plan, cudaStream_t st) {
     if (plan.precision == GP_FP32) {
       ATensorArgs<float> a{etab, vt, (float*)plan.a_tensor, plan.n_freq, h.M, C, J, h.d, plan.tr3 ? 1 : 0};
       k_build_a_f32<<<nb, 128, 0, st>>>(a);
+    } else if (plan.precision == GP_DF64) {
+      ATensorArgs<dd> a{etab, vt, (dd*)plan.a_tensor, plan.n_freq, h.M, C, J, h.d, plan.tr3 ? 1 : 0};
+      k_build_a_dd<<<nb, 128, 0, st>>>(a);
     } else {
       ATensorArgs<double> a{etab, vt, (double*)plan.a_tensor, plan.n_freq, h.M, C, J, h.d, plan.tr3 ? 1 : 0};
       k_build_a_f64<<<nb, 128, 0, st>>>(a);

@@ -139,6 +139,7 @@ struct Plan {
   bool tr3 = false;
   int t3_rb = 1;                        // grid rows per CTA of the row kernels
   void* tw_half = nullptr;              // two-level twiddle tables of the row kernels
+  void* col_tw = nullptr;               // pass tables of the float-float column transforms
   std::map<int, cufftHandle> fft_t3;    // contiguous column C2C plans keyed by R
   cufftHandle t3_plan(int R);
   long long bytes = 0;
@@ -255,7 +256,7 @@ void rowfft_forward(Plan& plan, int R, cudaStream_t st);
 void rowfft_diag(Plan& plan, int R, cudaStream_t st);
 void rowfft_inverse(Plan& plan, int R, cudaStream_t st);
 // transposed pruned transforms (d = 2, nf = 2^a)
-bool tr3_supported(int d, long long nf, size_t rs);
+bool tr3_supported(int d, long long nf, int precision);
 void tr3_setup(Plan& plan);
 void tr3_forward(Plan& plan, int R, cudaStream_t st);
 void tr3_diag(Plan& plan, int R, cudaStream_t st);

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <vector>
 
+#include "ff64.h"
 #include "plan.h"
 
 namespace gpn {
@@ -343,6 +344,10 @@ void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double*
         k_gather_points<float><<<blocks_for(n, 256), 256, 0, st>>>(
             ps.perm, n, d, l0_tmp, xi_tmp, ps.cell0[0], ps.cell0[1], ps.cell0[2], (float*)ps.xi[0], (float*)ps.xi[1],
             (float*)ps.xi[2], w_dev, sig_dev, cb, (float*)ps.wk, ps.wabs);
+      else if (plan.precision == GP_DF64)
+        k_gather_points<dd><<<blocks_for(n, 256), 256, 0, st>>>(
+            ps.perm, n, d, l0_tmp, xi_tmp, ps.cell0[0], ps.cell0[1], ps.cell0[2], (dd*)ps.xi[0], (dd*)ps.xi[1],
+            (dd*)ps.xi[2], w_dev, sig_dev, cb, (dd*)ps.wk, ps.wabs);
       else
         k_gather_points<double><<<blocks_for(n, 256), 256, 0, st>>>(
             ps.perm, n, d, l0_tmp, xi_tmp, ps.cell0[0], ps.cell0[1], ps.cell0[2], (double*)ps.xi[0],

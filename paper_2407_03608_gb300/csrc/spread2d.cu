@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "fft_core.h"
 #include "kernels.h"
 
 namespace gpn {
@@ -73,7 +74,9 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
   constexpr int TY = kWarps * RPW;
   constexpr int WP = wk_pitch<T>(NC);
   constexpr int VW = (int)(16 / sizeof(T));
-  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  // 16-byte vector of VW values: four floats, two doubles or two float-float values
+  using V = typename std::conditional<sizeof(T) == 4, float4,
+                                      typename std::conditional<is_dd<T>::value, fft::cpx<dd>, double2>::type>::type;
   const int PSX = col_stride(a.width), SY = row_stride(a.width, RPW);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_wk = reinterpret_cast<T*>(smem_raw);                      // [kSlots][WP]
@@ -179,10 +182,10 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
       const T yq = a.xiy[p], xq = a.xix[p];
       T* py = s_psy + slot * SY;
       T* px = s_psx + slot * PSX;
-      for (int j = 0; j < W; ++j) px[j] = es_psi<T>((T)j - xq, a.beta, a.inv_halfw);
+      for (int j = 0; j < W; ++j) px[j] = psi_at<T>(j, xq, a.beta, a.inv_halfw);
       for (int j = 0; j < SY; ++j) {
         const int jj = j - (RPW - 1);
-        py[j] = (jj >= 0 && jj < W) ? es_psi<T>((T)jj - yq, a.beta, a.inv_halfw) : T(0);
+        py[j] = (jj >= 0 && jj < W) ? psi_at<T>(jj, yq, a.beta, a.inv_halfw) : T(0);
       }
       const T amp = (T)alpha_r[p];
       const T* wkp = a.wk + (size_t)p * C;
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
       for (int rr = 0; rr < RPW; ++rr) {
         const T v = px * pyr[rr];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) acc[rr][k] += v * wk[k];
+        for (int k = 0; k < NC; ++k) madd(acc[rr][k], v, wk[k]);
       }
     }
     __syncthreads();  // slots, lists and counters are refilled by the next round
@@ -360,6 +363,8 @@ void build_spread2d_tiles(Plan& plan, const std::vector<int>& bstart) {
 void launch_spread2d(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
   if (plan.precision == GP_FP32)
     impl<float>(plan, alpha_sorted, R, st);
+  else if (plan.precision == GP_DF64)
+    impl<dd>(plan, alpha_sorted, R, st);
   else
     impl<double>(plan, alpha_sorted, R, st);
 }

@@ -5,7 +5,8 @@
 //
 // stdin:  mode L count, then the input numbers (mode c2c/ic2c: 2*2^L reals as
 //         interleaved complex; r2c: 2^(L+1) reals; c2r: 2*(2^L + 1) reals, the half
-//         spectrum X[0..N2]).  fc2c/fic2c: c2c/ic2c in float (the FP32 plans' arithmetic).
+//         spectrum X[0..N2]).  fc2c/fic2c: c2c/ic2c in float (the FP32 plans' arithmetic);
+//         dc2c/dic2c: in float-float (the GP_DF64 plans' arithmetic, ff64.h).
 // stdout: the output numbers, one per line (c2c/ic2c: 2*2^L; r2c: 2*(2^L + 1);
 //         c2r: 2^(L+1) reals).
 #include <cmath>
@@ -120,6 +121,22 @@ int main() {
     else
       fft<false, float>(fb, L);
     for (int i = 0; i < N; ++i) std::printf("%.9g\n%.9g\n", fb[gpn::fft::pad(i)].x, fb[gpn::fft::pad(i)].y);
+    return 0;
+  }
+  if (!std::strcmp(mode, "dc2c") || !std::strcmp(mode, "dic2c")) {
+    using gpn::dd;
+    std::vector<cpx<dd>> fb(gpn::fft::pad(N) + 1, cpx<dd>{dd(0.0), dd(0.0)});
+    for (int i = 0; i < N; ++i) {
+      double re, im;
+      if (std::scanf("%lf %lf", &re, &im) != 2) return 1;
+      fb[gpn::fft::pad(i)] = {dd(re), dd(im)};
+    }
+    if (mode[1] == 'i')
+      fft<true, dd>(fb, L);
+    else
+      fft<false, dd>(fb, L);
+    for (int i = 0; i < N; ++i)
+      std::printf("%.17g\n%.17g\n", (double)fb[gpn::fft::pad(i)].x, (double)fb[gpn::fft::pad(i)].y);
     return 0;
   }
   if (!std::strcmp(mode, "c2cr")) {

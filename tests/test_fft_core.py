@@ -18,8 +18,10 @@ CSRC = os.path.join(ROOT, "paper_2407_03608_gb300", "csrc")
 @pytest.fixture(scope="module")
 def host_prog(tmp_path_factory):
     exe = tmp_path_factory.mktemp("fft") / "fft_core_check"
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", CSRC, os.path.join(ROOT, "tests", "fft_core_check.cpp"),
-                           "-o", str(exe)])
+    # no floating-point contraction: the float-float steps rely on every product and sum
+    # being rounded on its own
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", CSRC,
+                           os.path.join(ROOT, "tests", "fft_core_check.cpp"), "-o", str(exe)])
     return str(exe)
 
 
@@ -93,3 +95,18 @@ def test_real_split_matches_rfft_and_irfft(host_prog, L):
     y = run(host_prog, "c2r", L, inter)              # z[n] = x[2n] + i x[2n+1]
     ref = np.fft.irfft(X, nf) * nf                # unnormalised C2R
     assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("L", [5, 8, 12, 13])
+def test_float_float_passes(host_prog, L):
+    """The passes in float-float (the GP_DF64 plans' arithmetic, two float words a value)
+    reach float64-grade accuracy: within 1e-13 of numpy's transform, elementwise relative
+    to the largest output, where plain float stays near 1e-7."""
+    n = 1 << L
+    rng = np.random.default_rng(400 + L)
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    inter = np.column_stack([z.real, z.imag]).ravel()
+    for mode, ref in (("dc2c", np.fft.fft(z)), ("dic2c", np.fft.ifft(z) * n)):
+        f = run(host_prog, mode, L, inter)
+        got = f[0::2] + 1j * f[1::2]
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref)), mode

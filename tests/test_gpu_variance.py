@@ -14,7 +14,7 @@ from oracle import kernel as okern
 from oracle import ktilde
 from oracle import variance
 
-from test_gpu_matvec import explicit_params, plan_kwargs, rel
+from test_gpu_matvec import explicit_params, plan_kwargs, rel, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -68,4 +68,5 @@ def test_variance_many_probes_in_chunks(gpn):
     ref = variance.variance_probes(Kt, eta2, Z)
     var, info = plan.posterior_variance(Z, eta2, rtol=1e-13, maxit=20000)
     assert rel(var, ref) <= 1e-8, rel(var, ref)
-    assert rel(var, variance.variance_exact(Kt, eta2)) <= 0.10
+    # the estimator's scatter is per entry, so this bound is on the l2 norm only
+    assert rel_l2(var, variance.variance_exact(Kt, eta2)) <= 0.10

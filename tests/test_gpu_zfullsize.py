@@ -3,11 +3,14 @@
 The workloads are too large for the dense oracle, so the GPU matvec is compared with
 the oracle's exact rows of K alpha (Eq. nonstat2, direct sums over all N points) on
 seeded samples of rows:
-  * 2-D clustered, N = 1e6, Matern 3/2, eps = 1e-6, FP32 plan: sampled rows within the
-    FP32 bar 1e-4 (measured about 1e-6), and the whole vector within 1e-4 of the FP64
-    plan on the same parameters;
+  * 2-D clustered, N = 1e6, Matern 3/2, eps = 1e-6: the FP64 plan's sampled rows within
+    the FP64 bar 1e-6; the FP32 plan's sampled rows within 2e-6 (the bench measures about
+    1e-6); the FP32 plan's whole vector within 1e-6 of the FP64 plan on the same
+    parameters (the metric's condition for the mixed-precision path);
   * 3-D uniform, N = 2e6, Matern 5/2, eps = 1e-6, FP32 plan (about 100 GB resident):
     sampled rows within 1e-4.
+Each bar holds for the relative l2 error and for the largest error relative to the
+largest entry (``rel``).
 The file sorts after the other GPU tests so that their plans are gone when these large
 ones are built; a test is skipped when the device has less free memory than it needs.
 """
@@ -20,6 +23,8 @@ import torch
 import gpinputs
 from oracle import kernel as okern
 from oracle import rows as orows
+
+from test_gpu_matvec import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +40,7 @@ def _rows_error(w, got, n_rows, seed):
     wp, sig = okern.paper_fields(w.s, w.l, w.d)
     idx = np.random.default_rng(seed).choice(w.N, size=n_rows, replace=False)
     ref = orows.rows(w.points, wp, sig, w.nu, w.alpha, idx)
-    return float(np.linalg.norm(got[idx] - ref) / np.linalg.norm(ref))
+    return rel(got[idx], ref)
 
 
 def _plan(gpn, w, precision, **kw):
@@ -59,10 +64,12 @@ def test_two_dimensional_benchmark_workload(gpn):
             p64.close()
     finally:
         p32.close()
+    e_rows64 = _rows_error(w, got64, 1024, seed=31)
+    assert e_rows64 <= 1e-6, e_rows64
     e_rows = _rows_error(w, got, 1024, seed=31)
-    assert e_rows <= 1e-4, e_rows
-    e_64 = float(np.linalg.norm(got - got64) / np.linalg.norm(got64))
-    assert e_64 <= 1e-4, e_64
+    assert e_rows <= 2e-6, e_rows
+    e_64 = rel(got, got64)
+    assert e_64 <= 1e-6, e_64
 
 
 def test_three_dimensional_workload(gpn):
