@@ -53,7 +53,8 @@ def test_df64_matches_fp64_plan(gpn, eps):
     2^13-point column kernel); the same parameters on a GP_FP64 plan."""
     w = gpinputs.config_2d(20_000, 1.5)
     dd_plan = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=eps, precision=gpn.GP_DF64, max_rhs=2)
-    f64 = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=eps, precision=gpn.GP_FP64, **dd_plan.matched_opts())
+    f64 = gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=eps, precision=gpn.GP_FP64, max_rhs=2,
+                   **dd_plan.matched_opts())
     assert dd_plan.info["nf"] == f64.info["nf"] and dd_plan.info["M"] == f64.info["M"]
     A = gpinputs.random_alpha(w.N, 2, seed=13)
     got = dd_plan.matvec(torch.from_numpy(A).cuda()).cpu().numpy()
