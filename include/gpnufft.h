@@ -133,6 +133,13 @@ typedef struct gp_plan_opts {
                              on the caller's stream, keep the fastest.  Tiles and bins are
                              the same size, so this tunes both.  Holds two plans at a time;
                              ignored when GP_SET_TILE is set.                            */
+  int rhs_block;          /* right-hand sides per pass through the fine grids and spectra
+                             (0 = max_rhs): the plan holds grids, spectra and transform
+                             buffers for rhs_block right-hand sides and the CG vectors for
+                             max_rhs; a matvec or CG iteration with R > rhs_block runs steps
+                             (1)-(5) over the columns in blocks of rhs_block, one after the
+                             other on the caller's stream, so R up to max_rhs fits where
+                             max_rhs sets of grids would not.                             */
 } gp_plan_opts;
 
 typedef struct gp_plan_info {
@@ -153,6 +160,7 @@ typedef struct gp_plan_info {
   int diag_correct;                        /* 1 when the diagonal defect is added         */
   int tuned;                               /* plans the autotuner timed (0: not tuned)    */
   double tune_ms;                          /* this plan's matvec time in the autotuner    */
+  int rhs_block;                           /* right-hand sides per pass through the grids */
 } gp_plan_info;
 
 /* The autotuner's search space (host only, no GPU needed): every spread/interp tile

@@ -283,7 +283,7 @@ void make_tensor_map(Plan& plan) {
   cuuint64_t dims[4], strides[3];
   cuuint32_t box[4], es[4] = {1, 1, 1, 1};
   for (int q = 0; q < d; ++q) dims[q] = (cuuint64_t)h.nf;
-  dims[d] = (cuuint64_t)plan.geom.C * plan.max_rhs;
+  dims[d] = (cuuint64_t)plan.geom.C * plan.grid_rhs;
   cuuint64_t st = rs;
   for (int q = 0; q < d; ++q) {
     st *= (cuuint64_t)h.nf;
@@ -387,8 +387,11 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   ps.a_bytes = (long long)(C * (C + 1) / 2) * nfreq * (long long)rs;
   ps.lean_bytes = J * (h.M + 1) * lean_channel_pitch(C, rs) * (long long)rs;
   // the large allocations: spreading and interpolation grids, spectra or the pruned
-  // transforms' column buffers, per-point data and the nine work vectors
-  const long long CR = (long long)C * max_rhs;
+  // transforms' column buffers (for a block of rhs_block right-hand sides), per-point data
+  // and the nine work vectors (for max_rhs)
+  GPN_CHECK(o.rhs_block >= 0, GP_EINVAL, "rhs_block must be >= 0");
+  const int grid_rhs = (o.rhs_block > 0 && o.rhs_block < max_rhs) ? o.rhs_block : max_rhs;
+  const long long CR = (long long)C * grid_rhs;
   const long long spectra = (ps.tr3 || ps.rowfft) ? 3 * (d == 2 ? h.nf : 1) * CR * (h.M + 1) * 2 * (long long)rs
                                                   : CR * S * 2 * (long long)rs;
   ps.est_rest = 2 * CR * G * (long long)rs + spectra + N * (long long)(d * (4 + rs) + 8 + C * rs) +
@@ -436,6 +439,8 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->param_mode = o.param_mode;
   plan->N = N;
   plan->max_rhs = max_rhs;
+  plan->grid_rhs = (o.rhs_block > 0 && o.rhs_block < max_rhs) ? o.rhs_block : max_rhs;
+  const int grid_rhs = plan->grid_rhs;
   plan->max_bytes = o.max_bytes;
   plan->real_size = o.precision == GP_FP32 ? 4 : 8;
 
@@ -493,14 +498,14 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
     plan->a_tensor = plan->alloc((size_t)a_bytes);
     build_a_tensor(*plan, st);
   }
-  plan->grid = plan->alloc((size_t)C * max_rhs * G * rs);
-  GPN_CUDA(cudaMemsetAsync(plan->grid, 0, (size_t)C * max_rhs * G * rs, st));
-  plan->grid_out = plan->alloc((size_t)C * max_rhs * G * rs);
-  GPN_CUDA(cudaMemsetAsync(plan->grid_out, 0, (size_t)C * max_rhs * G * rs, st));
+  plan->grid = plan->alloc((size_t)C * grid_rhs * G * rs);
+  GPN_CUDA(cudaMemsetAsync(plan->grid, 0, (size_t)C * grid_rhs * G * rs, st));
+  plan->grid_out = plan->alloc((size_t)C * grid_rhs * G * rs);
+  GPN_CUDA(cudaMemsetAsync(plan->grid_out, 0, (size_t)C * grid_rhs * G * rs, st));
   if (plan->rowfft || plan->tr3) {
     set_data_extent(*plan);
     const size_t rows = d == 2 ? (size_t)h.nf : 1;
-    const size_t fbytes = rows * C * (size_t)max_rhs * (h.M + 1) * 2 * rs;
+    const size_t fbytes = rows * C * (size_t)grid_rhs * (h.M + 1) * 2 * rs;
     plan->fx = plan->alloc(fbytes);
     plan->fy = plan->alloc(fbytes);
     plan->fz = plan->alloc(fbytes);
@@ -511,7 +516,7 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
     else
       build_twiddles(*plan);
   } else {
-    plan->spec = plan->alloc((size_t)C * max_rhs * S * 2 * rs);
+    plan->spec = plan->alloc((size_t)C * grid_rhs * S * 2 * rs);
   }
   plan->interp_cc = (int)std::max<size_t>(
       1, std::min<size_t>((size_t)C, kInterpSmemBudget / interp_stage_bytes(d, h.tile, h.width, rs)));
@@ -953,6 +958,7 @@ int gp_plan_params(int d, long long N, double nu, double eps, double scale_min, 
     info->transform = ps.tr3 ? 3 : (ps.rowfft ? 2 : 1);
     info->bytes_resident = ps.est;
     info->max_rhs = o.max_rhs > 0 ? o.max_rhs : 1;
+    info->rhs_block = (o.rhs_block > 0 && o.rhs_block < info->max_rhs) ? o.rhs_block : info->max_rhs;
     info->step3 = ps.lean ? 2 : 1;
     info->diag_correct = o.diag_correct ? 1 : 0;
     return GP_OK;
@@ -996,6 +1002,7 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->est_err_alias = h.est_alias;
     info->bytes_resident = p->bytes;
     info->max_rhs = p->max_rhs;
+    info->rhs_block = p->grid_rhs;
     info->step3 = p->lean ? 2 : 1;
     info->diag_correct = p->dcorr ? 1 : 0;
     info->tuned = p->tuned;

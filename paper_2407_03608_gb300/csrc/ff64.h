@@ -20,6 +20,8 @@
 // arithmetic; compile them without floating-point contraction.
 #pragma once
 
+#include <cmath>
+
 #ifdef __CUDACC__
 #define FF_HD __host__ __device__ __forceinline__
 #else
@@ -89,6 +91,17 @@ FF_HD dd operator*(dd a, dd b) {
   return fast_two_sum(p, e);
 }
 
+// a / b: the float quotient q = a.hi / b.hi refined by one correction, q + (a - q b) / b.hi,
+// with q b formed exactly (TwoProd); relative error a few u^2
+FF_HD dd operator/(dd a, dd b) {
+  using namespace ffops;
+  const float q = a.hi / b.hi;
+  const float p = mul(q, b.hi);
+  const float e = fma(q, b.hi, -p);                    // q b.hi = p + e exactly
+  const float r = sub(add(sub(sub(a.hi, p), e), a.lo), mul(q, b.lo));
+  return fast_two_sum(q, r / b.hi);
+}
+
 FF_HD dd& operator+=(dd& a, dd b) { return a = a + b; }
 FF_HD dd& operator-=(dd& a, dd b) { return a = a - b; }
 FF_HD dd& operator*=(dd& a, dd b) { return a = a * b; }
@@ -103,6 +116,61 @@ FF_HD dd fma_dd(dd a, dd b, dd c) {
   e = fma(a.lo, b.hi, e);
   const dd s = two_sum(p, c.hi);
   return fast_two_sum(s.hi, add(s.lo, add(e, c.lo)));
+}
+
+// A float-float constant from a double (folded at compile time)
+FF_HD constexpr dd ddc(double x) { return dd((float)x, (float)(x - (double)(float)x)); }
+
+// Square root of a non-negative float-float value: the float square root refined by one
+// Newton step, s + (a - s^2) / (2 s), with s^2 formed exactly by TwoProd (relative error
+// a few u^2).  Zero or negative inputs give zero.
+FF_HD dd sqrt_dd(dd a) {
+  using namespace ffops;
+  if (!(a.hi > 0.0f)) return dd(0.0f, 0.0f);
+  const float s = sqrtf(a.hi);
+  const float p = mul(s, s);
+  const float e = fma(s, s, -p);                       // s^2 = p + e exactly
+  const float r = add(sub(sub(a.hi, p), e), a.lo);     // a - s^2 (a.hi - p is exact: p ~ a.hi)
+  return fast_two_sum(s, r / add(s, s));
+}
+
+// e^u of a float-float value by range reduction: u = k ln 2 + r with k = round(u / ln 2),
+// r = u - k ln 2 in float-float (|r| <= ln(2)/2), then e^r = (e^(r/8))^8 with e^(r/8) from
+// its Taylor series to degree 9 (|r/8| < 0.044: the remainder is below 1e-20), three
+// squarings, and the exact scaling by 2^k.  Relative error about 1e-14 (the squarings
+// multiply the rounding of e^(r/8) by eight).  For the arguments used here, -60 < u <= 0.
+FF_HD dd exp_dd(dd u) {
+  using namespace ffops;
+  const float k = rintf(mul(u.hi, 1.44269504088896340736f));
+  const dd r0 = u - dd(k, 0.0f) * ddc(0.69314718055994530942);
+  const dd r = dd(ldexpf(r0.hi, -3), ldexpf(r0.lo, -3));
+  dd p = ddc(1.0 / 362880.0);                          // 1/9!
+  p = fma_dd(p, r, ddc(1.0 / 40320.0));
+  p = fma_dd(p, r, ddc(1.0 / 5040.0));
+  p = fma_dd(p, r, ddc(1.0 / 720.0));
+  p = fma_dd(p, r, ddc(1.0 / 120.0));
+  p = fma_dd(p, r, ddc(1.0 / 24.0));
+  p = fma_dd(p, r, ddc(1.0 / 6.0));
+  p = fma_dd(p, r, dd(0.5f, 0.0f));
+  p = fma_dd(p, r, dd(1.0f, 0.0f));
+  p = fma_dd(p, r, dd(1.0f, 0.0f));
+  p = p * p;
+  p = p * p;
+  p = p * p;
+  const int ki = (int)k;
+  return dd(ldexpf(p.hi, ki), ldexpf(p.lo, ki));
+}
+
+// The exponential-of-semicircle spreading kernel psi(s) = exp(beta (sqrt(1 - z^2) - 1)),
+// z = s inv_halfw, at s = j - xi (integer cell offset j), in float-float.  The exponent is
+// formed as -beta z^2 / (1 + sqrt(1 - z^2)), which avoids the cancellation of
+// sqrt(1 - z^2) - 1 near z = 0.  Zero outside |z| < 1.
+FF_HD dd es_psi_dd(int j, dd xi, dd beta, dd inv_halfw) {
+  const dd z = (dd((float)j, 0.0f) - xi) * inv_halfw;
+  const dd z2 = z * z;
+  const dd q = dd(1.0f, 0.0f) - z2;
+  if (!(q.hi > 0.0f)) return dd(0.0f, 0.0f);
+  return exp_dd(-(beta * z2) / (sqrt_dd(q) + dd(1.0f, 0.0f)));
 }
 
 }  // namespace gpn

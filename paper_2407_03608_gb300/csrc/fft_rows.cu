@@ -145,7 +145,7 @@ struct RowArgs {
   long long M;
   int L;                         // log2(nf / 2)
   int CR;                        // channels in use (C * R)
-  int CP;                        // channel pitch of the compact layout (C * max_rhs)
+  int CP;                        // channel pitch of the compact layout (C * grid_rhs)
   int row_lo;                    // first grid row handled (d = 2); 0 for d = 1
   int col_lo, col_hi;            // columns that may hold data / that interp reads
   int d;
@@ -220,7 +220,7 @@ struct DiagCArgs {
   long long n_freq;
   int C;
   int R;
-  int CP;                            // channel pitch (C * max_rhs)
+  int CP;                            // channel pitch (C * grid_rhs)
   int d;
 };
 
@@ -271,7 +271,7 @@ RowArgs<T> row_args(Plan& plan, int R) {
   a.M = plan.geom.M;
   a.L = plan.fft_log2h;
   a.CR = plan.geom.C * R;
-  a.CP = plan.geom.C * plan.max_rhs;
+  a.CP = plan.geom.C * plan.grid_rhs;
   a.row_lo = plan.row_lo;
   a.col_lo = plan.col_lo;
   a.col_hi = plan.col_hi;
@@ -317,7 +317,7 @@ void diag_impl(Plan& plan, int R, cudaStream_t st) {
   a.n_freq = plan.n_freq;
   a.C = plan.geom.C;
   a.R = R;
-  a.CP = plan.geom.C * plan.max_rhs;
+  a.CP = plan.geom.C * plan.grid_rhs;
   a.d = plan.geom.d;
   dim3 grid((unsigned)blocks_for(a.M + 1, 128), (unsigned)(two ? 2 * a.M + 1 : 1));
   switch (cmax_bucket(a.C)) {
@@ -411,9 +411,9 @@ void build_twiddles(Plan& plan) {
 cufftHandle Plan::col_plan(int R) {
   auto it = fft_col.find(R);
   if (it != fft_col.end()) return it->second;
-  // columns of all used channels are adjacent (idist 1); rows are C*max_rhs*(M+1) apart
+  // columns of all used channels are adjacent (idist 1); rows are C*grid_rhs*(M+1) apart
   int n[1] = {(int)geom.nf};
-  const int pitch = geom.C * max_rhs * (int)(geom.M + 1);
+  const int pitch = geom.C * grid_rhs * (int)(geom.M + 1);
   const int cols = geom.C * R * (int)(geom.M + 1);
   cufftHandle hdl;
   GPN_CUFFT2(cufftPlanMany(&hdl, 1, n, n, pitch, 1, n, pitch, 1, precision == GP_FP32 ? CUFFT_C2C : CUFFT_Z2Z, cols));

@@ -57,17 +57,16 @@ inline T es_beta_arg(double beta) {
 }
 
 // psi(j - xi) at the integer cell offset j.  Float-float plans evaluate the kernel in
-// float64 (exp and sqrt to double precision) and round it to float-float: the offset
-// xi is exact in both words, and the kernel values then carry about 1e-16 relative
-// error, far below the float-float rounding of the sums they enter.
+// float-float on the FP32 pipe (es_psi_dd of ff64.h: within about 5e-14 of psi(0) = 1),
+// not with the float64 exp, which on GB300 made the kernel values the largest cost of the
+// spread and the interpolation.
 template <typename T>
 __device__ __forceinline__ T psi_at(int j, T xi, T beta, T inv_halfw) {
   return es_psi<T>((T)j - xi, beta, inv_halfw);
 }
 template <>
 __device__ __forceinline__ dd psi_at<dd>(int j, dd xi, dd beta, dd inv_halfw) {
-  const double s = ((double)j - (double)xi.hi) - (double)xi.lo;
-  return dd(es_psi<double>(s, (double)beta, (double)inv_halfw));
+  return es_psi_dd(j, xi, beta, inv_halfw);
 }
 
 // Warp shuffles of plan values (a float-float value moves as its two words).

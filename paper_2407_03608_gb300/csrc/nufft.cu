@@ -9,6 +9,7 @@
 // folded into A' = A / psihat^2.
 #include <cufft.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "ff64.h"
@@ -187,7 +188,9 @@ void PhaseProfile::destroy() {
   created = false;
 }
 
-void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st) {
+namespace {
+// steps (1)-(5) for R <= grid_rhs right-hand sides (one pass through the grids)
+void matvec_block(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st) {
   PhaseProfile& pf = plan.prof;
   const bool rec = pf.on;
   if (rec) {
@@ -213,6 +216,17 @@ void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, i
     pf.in_matvec = false;
     GPN_CUDA(cudaEventRecord(pf.ev[5], st));
     pf.pending = true;
+  }
+}
+}  // namespace
+
+// Columns beyond the grids' rhs_block run in blocks, one after the other on the stream
+// (each block is one recorded pass when the phases are profiled).
+void matvec_sorted(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, double shift, cudaStream_t st) {
+  const size_t n = (size_t)plan.N;
+  for (int r0 = 0; r0 < R; r0 += plan.grid_rhs) {
+    const int rc = std::min(plan.grid_rhs, R - r0);
+    matvec_block(plan, alpha_sorted + (size_t)r0 * n, out_sorted + (size_t)r0 * n, rc, shift, st);
   }
 }
 

@@ -74,6 +74,7 @@ struct Plan {
   int param_mode = GP_PARAMS_SCALES;
   long long N = 0;
   int max_rhs = 1;
+  int grid_rhs = 1;                     // right-hand sides the grids and spectra hold (rhs_block)
   long long max_bytes = 0;
   Hyper h;
   Tables tb;

@@ -123,6 +123,24 @@ int main() {
     for (int i = 0; i < N; ++i) std::printf("%.9g\n%.9g\n", fb[gpn::fft::pad(i)].x, fb[gpn::fft::pad(i)].y);
     return 0;
   }
+  if (!std::strcmp(mode, "dpsi")) {
+    // float-float ES kernel (es_psi_dd, as the GP_DF64 kernels evaluate it): "dpsi W"
+    // then beta and count, then (j, xi) pairs; prints exp(beta (sqrt(1 - z^2) - 1)),
+    // z = (j - xi) 2 / W
+    using gpn::dd;
+    double beta;
+    int n;
+    if (std::scanf("%lf %d", &beta, &n) != 2) return 1;
+    const dd b(beta), ih(2.0 / L);
+    for (int i = 0; i < n; ++i) {
+      int j;
+      double xi;
+      if (std::scanf("%d %lf", &j, &xi) != 2) return 1;
+      const dd v = gpn::es_psi_dd(j, dd(xi), b, ih);
+      std::printf("%.17g\n", (double)v);
+    }
+    return 0;
+  }
   if (!std::strcmp(mode, "dc2c") || !std::strcmp(mode, "dic2c")) {
     using gpn::dd;
     std::vector<cpx<dd>> fb(gpn::fft::pad(N) + 1, cpx<dd>{dd(0.0), dd(0.0)});

@@ -110,3 +110,27 @@ def test_float_float_passes(host_prog, L):
         f = run(host_prog, mode, L, inter)
         got = f[0::2] + 1j * f[1::2]
         assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref)), mode
+
+
+@pytest.mark.parametrize("W,beta", [(9, 20.6), (13, 30.1), (16, 37.0)])
+def test_float_float_kernel_values(host_prog, W, beta):
+    """The exponential-of-semicircle kernel in float-float (sqrt_dd, exp_dd) against float64:
+    within 5e-14 of psi(0) = 1 everywhere, and within 2e-13 relative where psi >= 1e-3 (near
+    the ends of the support 1 - z^2 is formed with cancellation in either arithmetic)."""
+    # the plans' offsets: xi = g - l0 with l0 = ceil(g - W/2), so xi in (W/2 - 1, W/2]
+    rng = np.random.default_rng(W)
+    j = rng.integers(0, W, 400)
+    xi = W / 2.0 - rng.random(400)
+    xi[:4] = W / 2.0 - np.array([0.0, 1e-12, 0.5, 1.0 - 1e-9])
+    inp = "%.17g %d\n" % (beta, len(j)) + "\n".join("%d %.17g" % (a, b) for a, b in zip(j, xi)) + "\n"
+    out = subprocess.run([host_prog], input="dpsi %d\n" % W + inp, capture_output=True, text=True,
+                         check=True).stdout
+    got = np.array([float(v) for v in out.split()])
+    z = (j - xi) * 2.0 / W
+    q = 1.0 - z * z
+    ref = np.where(q > 0, np.exp(beta * (np.sqrt(np.maximum(q, 0.0)) - 1.0)), 0.0)
+    inside = ref > 0
+    assert np.all(got[~inside] == 0.0)
+    assert np.max(np.abs(got - ref)) <= 5e-14
+    big = ref >= 1e-3
+    assert np.max(np.abs(got[big] - ref[big]) / ref[big]) <= 2e-13

@@ -240,3 +240,18 @@ def test_scale_range_is_taken_in_the_plans_parametrisation(abi):
         assert a[k] == b[k], k
     assert a["sigma_lo"] == pytest.approx(b["sigma_lo"], rel=1e-15)
     assert a["sigma_hi"] == pytest.approx(b["sigma_hi"], rel=1e-15)
+
+
+def test_rhs_block_keeps_one_block_of_grids(abi):
+    # grids, spectra and transform buffers for rhs_block right-hand sides, vectors for max_rhs
+    base = params(abi, 2, 100_000, 1e-5, 0.01, 0.02, max_rhs=1)
+    full = params(abi, 2, 100_000, 1e-5, 0.01, 0.02, max_rhs=64)
+    blocked = params(abi, 2, 100_000, 1e-5, 0.01, 0.02, max_rhs=64, rhs_block=8)
+    assert blocked["rhs_block"] == 8 and full["rhs_block"] == 64 and base["rhs_block"] == 1
+    per_rhs_grids = (full["bytes_resident"] - base["bytes_resident"]) / 63.0
+    assert blocked["bytes_resident"] < full["bytes_resident"] - 50 * per_rhs_grids
+    eight = params(abi, 2, 100_000, 1e-5, 0.01, 0.02, max_rhs=8)
+    # the same grids as max_rhs = 8, plus 56 more columns of the nine work vectors
+    assert blocked["bytes_resident"] - eight["bytes_resident"] == 100_000 * 56 * 8 * 9
+    # a block at least max_rhs is no block
+    assert params(abi, 2, 100_000, 1e-5, 0.01, 0.02, max_rhs=4, rhs_block=9)["rhs_block"] == 4
