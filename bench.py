@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the side measurements (config 1 latency, batched R, config 3, served solves)")
-    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--profile-case", action="store_true",
                     help="a fixed workload for profilers: build one plan (--d, --n, --eps, --precision, "
                          "--transform) and run --matvecs matvecs, nothing else")
@@ -586,26 +586,31 @@ def measure_config1(dev):
                               "inner_iters": int(ref_its[-1]), "rel_diff_vs_fp64_cg": ref_err}}
 
 
-def measure_batched(dev, n, R=8, steps=3):
-    """The 2-D clustered workload with R right-hand sides per CG iteration (8 noisy y vectors)."""
+def measure_batched(dev, n, block=8, steps=2):
+    """The batched workload: the 2-D clustered points, 64 right-hand sides (8 noisy y vectors
+    plus 56 +-1 probes), FP32 spread/FFT/step 3/interp with float64 CG reductions.  All 64
+    columns share each CG iteration (one gp_cg_solve call, graph-captured blocks of
+    iterations); the plan holds grids for `block` columns and runs steps (1)-(5) block after
+    block (rhs_block), so 64 columns fit where 64 sets of grids (about 640 GB) would not."""
     import torch
     import gpinputs
     import paper_2407_03608_gb300 as gpn
     from paper_2407_03608_gb300 import abi
-    w = gpinputs.config_2d(n, 1.5)
+    w = gpinputs.config_2d_batched(n)
+    R = w.y.shape[1]
     plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
-                    torch.from_numpy(w.l).to(dev), nu=1.5, eps=1e-6, precision=gpn.GP_FP32, max_rhs=R)
-    rng = np.random.default_rng(10)
-    Y = torch.from_numpy(np.ascontiguousarray(
-        (w.y[:, None] + 0.05 * rng.standard_normal((w.N, R))).T)).to(dev)   # (R, N) = column-major N x R
+                    torch.from_numpy(w.l).to(dev), nu=1.5, eps=1e-6, precision=gpn.GP_FP32, max_rhs=R,
+                    rhs_block=block)
+    Y = torch.from_numpy(np.ascontiguousarray(w.y.T)).to(dev)   # (R, N) = column-major N x R
     X = torch.empty_like(Y)
-    abi.gp_cg_solve(plan.handle, Y, X, R, w.eta ** 2, 1e-30, 2)
+    abi.gp_cg_solve(plan.handle, Y, X, R, w.eta ** 2, 1e-30, 1)
     ms = _events_ms(lambda: abi.gp_cg_solve(plan.handle, Y, X, R, w.eta ** 2, 1e-30, steps), 1) / steps
     nbytes = plan.info["bytes_resident"]
     plan.close()
-    return {"workload": w.name, "R": R, "precision": "fp32 (f64 CG)", "ms_per_step": round(ms, 3),
-            "value": round(w.N * R / (ms * 1e-3) / 1e6, 3), "unit": "Mpts/s (N*R per CG iteration)",
-            "bytes_resident": int(nbytes)}
+    return {"workload": w.name, "R": R, "rhs_block": block, "precision": "fp32 (f64 CG)",
+            "ms_per_step": round(ms, 3), "value": round(w.N * R / (ms * 1e-3) / 1e6, 3),
+            "unit": "Mpts/s (N*R per CG iteration)", "bytes_resident": int(nbytes),
+            "columns": "8 noisy y (seeds 10-17) + 56 Rademacher probes (seed 18)"}
 
 
 def measure_config3(dev, steps=3):
@@ -642,20 +647,29 @@ def measure_config3(dev, steps=3):
                                   "bytes_resident": lean_bytes}}
 
 
-def measure_serving(n_requests):
-    """A bounded sample of the serving stream: solves to rtol 1e-8 (FP32 CG inside FP64
-    refinement), p50/p99 latency at 80% of the measured capacity."""
+def measure_serving(n_requests, n_models=12):
+    """A bounded sample of the serving stream: requests on `n_models` models (points, fields,
+    nu; popularity 1/k), solved to rtol 1e-8 (FP32 CG inside float64 refinement) with each
+    model's plans kept resident (PlanCache, 120 GB budget); p50/p99 latency at 80% of the
+    measured capacity, one request at a time and with continuous batching (3 slots); every
+    10th served solution compared with the plain float64 GPU solve."""
     import gpinputs
     from paper_2407_03608_gb300.serving import Server
-    reqs = gpinputs.serving_stream(n_requests, n_min=1000, n_max=50_000, dims=(1, 2), nus=(1.5, 2.5), max_rhs=4)
-    srv = Server(hbm_budget=120e9, eps_target=1e-6)
-    out = srv.serve(reqs, load=0.8)
+    reqs = gpinputs.serving_stream(n_requests, n_min=1000, n_max=20_000, dims=(1, 2, 3), nus=(0.5, 1.5, 2.5),
+                                   max_rhs=16, n_models=n_models)
+    srv = Server(hbm_budget=120e9, eps_target=1e-6, cache_plans=True)
+    out = srv.serve(reqs, load=0.8, check_every=10)
     out.pop("records")
-    # continuous batching: three requests in flight on their own streams, latency on the
-    # wall clock at 80% of the capacity measured that way
+    # the same stream again with a cold cache and no cache, and with three requests in flight
+    srv.cache.clear()
+    nocache = Server(hbm_budget=120e9, eps_target=1e-6, cache_plans=False)
+    cold = nocache.serve(reqs, load=0.8)
+    out["without_cache"] = {k: cold[k] for k in ("capacity_solves_per_s", "latency_p50_s", "latency_p99_s",
+                                                 "service_p50_s", "plan_share")}
     out["continuous_batching"] = srv.serve_batched(reqs, load=0.8, slots=3)
-    out["sample"] = ("%d requests of the serving stream (seed 100): N log-uniform in [1e3, 5e4], d in {1, 2}, "
-                     "nu in {3/2, 5/2}, R in 1..4" % n_requests)
+    srv.cache.clear()
+    out["sample"] = ("%d requests of the serving stream (seed 100) on %d models: N log-uniform in [1e3, 2e4], "
+                     "d in {1, 2, 3}, nu in {1/2, 3/2, 5/2}, R in 1..16" % (n_requests, n_models))
     return out
 
 

@@ -167,6 +167,7 @@ class Request:
     nu: float
     eta: float
     y: np.ndarray          # (N,) or (N, R)
+    model: int = -1        # requests with the same model share points, fields and nu (-1: its own)
 
 
 def _trig_series(x: np.ndarray, g: np.random.Generator, degree: int = 3) -> np.ndarray:
@@ -182,31 +183,52 @@ def _trig_series(x: np.ndarray, g: np.random.Generator, degree: int = 3) -> np.n
     return f / m if m > 0 else f
 
 
+def _serving_model(g: np.random.Generator, n_min: int, n_max: int, dims, nus):
+    n = int(round(np.exp(g.uniform(np.log(n_min), np.log(n_max)))))
+    d = int(g.choice(dims))
+    nu = float(g.choice(nus))
+    x = g.random((n, d))
+    l0 = 0.08 * (n / 1000.0) ** (-1.0 / d)
+    l0 = max(l0, {1: 0.004, 2: 0.02, 3: 0.05}[d])
+    l = l0 * (1.0 + 0.4 * _trig_series(x, g))
+    s = 1.0 + 0.3 * _trig_series(x, g)
+    return x, s, l, nu
+
+
 def serving_stream(n_requests: int = 2000, rate_hz: float = 50.0, n_min: int = 1000,
                    n_max: int = 1_000_000, seed: int = 100, max_rhs: int = 16,
-                   dims=(1, 2, 3), nus=(0.5, 1.5, 2.5)) -> List[Request]:
+                   dims=(1, 2, 3), nus=(0.5, 1.5, 2.5), n_models: int = 0) -> List[Request]:
     """Poisson arrivals; N log-uniform in [n_min, n_max]; seeded smooth fields.
 
     l(x) = l0 (1 + 0.4 g1(x)), s(x) = 1 + 0.3 g2(x) with g1, g2 random trigonometric
     series normalised to [-1, 1]; l0 shrinks like (N/1000)^(-1/d) so that each row
     of K keeps a bounded number of significant entries (the narrow scaling regime).
+    R in 1..max_rhs right-hand sides, uniform on [0, 1] (as in Sec. 6.2).
+
+    n_models = 0: every request is a model of its own.  n_models > 0: the models
+    (points, fields, nu) are drawn first, and each request solves new right-hand sides
+    on one of them, model k with probability proportional to 1 / (k + 1) (a few popular
+    models, a long tail), so that a server can keep the plans of the popular ones.
     """
     g = _rng(seed)
     t = 0.0
     out = []
+    models = [_serving_model(g, n_min, n_max, dims, nus) for _ in range(n_models)]
+    if n_models:
+        pop = 1.0 / np.arange(1, n_models + 1)
+        pop /= pop.sum()
     for rid in range(n_requests):
         t += g.exponential(1.0 / rate_hz)
-        n = int(round(np.exp(g.uniform(np.log(n_min), np.log(n_max)))))
-        d = int(g.choice(dims))
-        nu = float(g.choice(nus))
+        if n_models:
+            m = int(g.choice(n_models, p=pop))
+            x, s, l, nu = models[m]
+        else:
+            m = -1
+            x, s, l, nu = _serving_model(g, n_min, n_max, dims, nus)
+        n = x.shape[0]
         r = int(g.integers(1, max_rhs + 1))
-        x = g.random((n, d))
-        l0 = 0.08 * (n / 1000.0) ** (-1.0 / d)
-        l0 = max(l0, {1: 0.004, 2: 0.02, 3: 0.05}[d])
-        l = l0 * (1.0 + 0.4 * _trig_series(x, g))
-        s = 1.0 + 0.3 * _trig_series(x, g)
         y = g.random((n, r)) if r > 1 else g.random(n)
-        out.append(Request(rid, t, x, s, l, nu, 0.1, y))
+        out.append(Request(rid, t, x, s, l, nu, 0.1, y, m))
     return out
 
 

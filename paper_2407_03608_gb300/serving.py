@@ -33,6 +33,7 @@ import argparse
 import json
 import threading
 import time
+from collections import OrderedDict
 from dataclasses import dataclass
 from typing import List, Optional
 
@@ -55,6 +56,7 @@ class Served:
     iters: int
     relres: float
     bytes_resident: int
+    cache_hit: bool = False
 
 
 def _rhs(req) -> int:
@@ -100,8 +102,9 @@ def _plan_fitting(gpn, req, budget: int, eps_target: float, precision, extra: Op
     for eps in [e for e in EPS_LADDER if e >= eps_target * (1 - 1e-12)]:
         try:
             kw = dict(extra or {})
+            mr = kw.pop("max_rhs_override", _rhs(req))
             return gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=precision,
-                            max_rhs=_rhs(req), max_bytes=int(budget), **kw), eps
+                            max_rhs=mr, max_bytes=int(budget), **kw), eps
         except gpn.GPError as e:
             if e.status != gpn.abi.GP_ENOMEM:
                 raise
@@ -109,12 +112,117 @@ def _plan_fitting(gpn, req, budget: int, eps_target: float, precision, extra: Op
     raise last
 
 
+class PlanCache:
+    """Resident plans of the models served so far: the FP64 and FP32 plans of a model (its
+    sorted points, Chebyshev weights, A' and grids) stay on the device between the requests
+    that use it, keyed by (model, eps), within `budget` bytes.  Idle entries are evicted
+    least recently used first when a new one needs room; an entry in use is never evicted.
+    One request uses an entry at a time (a plan's calls must not overlap): a second
+    request for the same model waits for it."""
+
+    class Entry:
+        def __init__(self):
+            self.plans = None          # (hi, lo, eps)
+            self.bytes = 0
+            self.users = 0
+            self.ready = threading.Event()
+            self.use = threading.Lock()
+            self.error = None
+
+    def __init__(self, budget: int):
+        self.budget = int(budget)
+        self.lock = threading.Lock()
+        self.entries: "OrderedDict[tuple, PlanCache.Entry]" = OrderedDict()
+        self.bytes = 0
+        self.hits = 0
+        self.misses = 0
+        self.evictions = 0
+
+    def _evict_for(self, need: int):
+        # caller holds self.lock
+        for key in list(self.entries.keys()):
+            if self.bytes + need <= self.budget:
+                break
+            e = self.entries[key]
+            if e.users == 0 and e.ready.is_set():
+                del self.entries[key]
+                self.bytes -= e.bytes
+                self.evictions += 1
+                if e.plans is not None:
+                    hi, lo, _ = e.plans
+                    lo.close()
+                    hi.close()
+
+    def acquire(self, key, predicted: int, build):
+        """The entry for `key`, built by build() -> (hi, lo, eps) on a miss, locked for the
+        caller's exclusive use; returns (entry, hit).  Release with release()."""
+        with self.lock:
+            e = self.entries.get(key)
+            hit = e is not None
+            if hit:
+                self.entries.move_to_end(key)
+                self.hits += 1
+            else:
+                self.misses += 1
+                e = PlanCache.Entry()
+                self.entries[key] = e
+                self._evict_for(predicted)
+            e.users += 1
+        if not hit:
+            try:
+                hi, lo, eps = build()
+                e.plans = (hi, lo, eps)
+                e.bytes = int(hi.info["bytes_resident"] + lo.info["bytes_resident"])
+                with self.lock:
+                    self.bytes += e.bytes
+            except BaseException as err:
+                e.error = err
+                with self.lock:
+                    self.entries.pop(key, None)
+                    e.users -= 1
+                e.ready.set()
+                raise
+            e.ready.set()
+        else:
+            e.ready.wait()
+            if e.error is not None:
+                with self.lock:
+                    e.users -= 1
+                raise e.error
+        e.use.acquire()
+        return e, hit
+
+    def release(self, e):
+        e.use.release()
+        with self.lock:
+            e.users -= 1
+            self._evict_for(0)
+
+    def clear(self):
+        with self.lock:
+            for e in self.entries.values():
+                if e.plans is not None:
+                    hi, lo, _ = e.plans
+                    lo.close()
+                    hi.close()
+            self.entries.clear()
+            self.bytes = 0
+
+    def stats(self) -> dict:
+        return {"hits": self.hits, "misses": self.misses, "evictions": self.evictions,
+                "resident_bytes": self.bytes, "entries": len(self.entries)}
+
+
 class Server:
     """Serves requests on the current CUDA device, one after another (``serve``) or
-    several in flight on their own streams (``serve_concurrent``, ``serve_batched``)."""
+    several in flight on their own streams (``serve_concurrent``, ``serve_batched``).
+    With ``cache_plans`` the FP64/FP32 plans of each model stay resident between the
+    requests on that model (``PlanCache``, within the HBM budget); without it every
+    request builds its plans and frees them."""
 
     def __init__(self, hbm_budget: float = 120e9, eps_target: float = 1e-6, rtol: float = 1e-8,
-                 inner_rtol: float = 1e-4, maxit: int = 20000, outer_max: int = 20):
+                 inner_rtol: float = 1e-4, maxit: int = 20000, outer_max: int = 20, cache_plans: bool = False,
+                 max_rhs: int = 16, rhs_block: int = 4):
         import paper_2407_03608_gb300 as gpn
         self.gpn = gpn
         self.budget = int(hbm_budget)
@@ -123,20 +231,55 @@ class Server:
         self.inner_rtol = inner_rtol
         self.maxit = maxit
         self.outer_max = outer_max
+        # cached plans take any request on their model: max_rhs columns, grids for rhs_block
+        self.cache = PlanCache(self.budget) if cache_plans else None
+        self.max_rhs = max_rhs
+        self.rhs_block = rhs_block
 
-    def serve_one(self, req) -> Served:
-        import torch
+    def _build_pair(self, req, stream_handle=None):
+        """The FP64 (residual) and FP32 (inner CG) plans of a request at the finest eps that
+        fits, sized for any request on the same model when plans are cached."""
         gpn = self.gpn
+        extra = {} if stream_handle is None else {"stream": stream_handle}
+        if self.cache is not None:
+            extra.update(max_rhs_override=self.max_rhs, rhs_block=min(self.rhs_block, self.max_rhs))
+        start = predicted_eps(gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
+        hi, eps = _plan_fitting(gpn, req, self.budget // 2, max(start, self.eps_target), gpn.GP_FP64, extra=extra)
+        try:
+            kw = dict(extra)
+            mr = kw.pop("max_rhs_override", _rhs(req))
+            lo = gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=gpn.GP_FP32, max_rhs=mr,
+                          **kw, **hi.matched_opts())
+        except BaseException:
+            hi.close()
+            raise
+        return hi, lo, eps
+
+    def _plans(self, req, stream_handle=None):
+        """(hi, lo, eps, release, hit): the request's plans, from the cache when it has them."""
+        if self.cache is None:
+            hi, lo, eps = self._build_pair(req, stream_handle)
+
+            def release():
+                lo.close()
+                hi.close()
+            return hi, lo, eps, release, False
+        key = (req.model if req.model >= 0 else -1 - req.rid, self.eps_target)
+        eps0 = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target)
+        need = self.budget if eps0 is None else predicted_footprint(self.gpn.abi, req, eps0)
+        entry, hit = self.cache.acquire(key, need, lambda: self._build_pair(req, stream_handle))
+        hi, lo, eps = entry.plans
+        return hi, lo, eps, (lambda: self.cache.release(entry)), hit
+
+    def serve_one(self, req, keep_alpha: bool = False):
+        import torch
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         # admission by the host-side footprint prediction; building at that level can still
-        # run out of memory, so the ladder continues from there
-        start = predicted_eps(gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
-        hi, eps = _plan_fitting(gpn, req, self.budget // 2, max(start, self.eps_target), gpn.GP_FP64)
-        lo = None
+        # run out of memory, so the ladder continues from there (or the model's plans are
+        # already resident)
+        hi, lo, eps, release, hit = self._plans(req)
         try:
-            lo = gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=gpn.GP_FP32,
-                          max_rhs=_rhs(req), **hi.matched_opts())
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             y = np.asarray(req.y, dtype=np.float64)
@@ -148,26 +291,19 @@ class Server:
             relres = float(np.max(info["relres"]))
             nbytes = int(hi.info["bytes_resident"] + lo.info["bytes_resident"])
         finally:
-            if lo is not None:
-                lo.close()
-            hi.close()
-        return Served(req.rid, req.points.shape[0], req.points.shape[1], req.nu, _rhs(req), eps, t2 - t0, t1 - t0,
-                      t2 - t1, iters, relres, nbytes)
+            release()
+        rec = Served(req.rid, req.points.shape[0], req.points.shape[1], req.nu, _rhs(req), eps, t2 - t0, t1 - t0,
+                     t2 - t1, iters, relres, nbytes, hit)
+        return (np.asarray(alpha), rec) if keep_alpha else rec
 
     def solve_on(self, req, stream):
         """One request on `stream`, from the calling host thread, with no device-wide
         synchronisation (other requests may run on other streams meanwhile): the FP64 and
         FP32 plans at the admitted eps, then the refined solve.  Returns (alpha, Served)."""
-        gpn = self.gpn
         sh = stream.cuda_stream
         t0 = time.perf_counter()
-        start = predicted_eps(gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
-        hi, eps = _plan_fitting(gpn, req, self.budget // 2, max(start, self.eps_target), gpn.GP_FP64,
-                                extra={"stream": sh})
-        lo = None
+        hi, lo, eps, release, hit = self._plans(req, sh)
         try:
-            lo = gpn.Plan(req.points, req.s, req.l, nu=req.nu, eps=eps, precision=gpn.GP_FP32,
-                          max_rhs=_rhs(req), stream=sh, **hi.matched_opts())
             stream.synchronize()
             t1 = time.perf_counter()
             y = np.asarray(req.y, dtype=np.float64)
@@ -177,11 +313,9 @@ class Server:
             t2 = time.perf_counter()
             nbytes = int(hi.info["bytes_resident"] + lo.info["bytes_resident"])
         finally:
-            if lo is not None:
-                lo.close()
-            hi.close()
+            release()
         rec = Served(req.rid, req.points.shape[0], req.points.shape[1], req.nu, _rhs(req), eps, t2 - t0, t1 - t0,
-                     t2 - t1, int(np.max(info["iters"])), float(np.max(info["relres"])), nbytes)
+                     t2 - t1, int(np.max(info["iters"])), float(np.max(info["relres"])), nbytes, hit)
         return np.asarray(alpha), rec
 
     def serve_concurrent(self, requests, slots: int = 3, arrivals=None):
@@ -236,11 +370,37 @@ class Server:
             "service_p99_s": float(np.percentile(service, 99)),
             "max_in_flight": int(info["max_inflight"]),
             "max_relres": float(max(r[1].relres for r in res)),
+            "cache_hit_rate": float(np.mean([r[1].cache_hit for r in res])),
         }
 
-    def serve(self, requests, load: float = 0.8) -> dict:
-        """Serve all requests; latency statistics at `load` times the measured capacity."""
-        done: List[Served] = [self.serve_one(r) for r in requests]
+    def check_vs_fp64(self, req, alpha, columns: int = 2, rtol: float = 1e-10) -> float:
+        """Largest relative error of served columns against the plain float64 GPU path on
+        the same plan parameters: plain CG (no refinement, one right-hand side at a time)
+        with the request's FP64 plan, to `rtol`.  Uses the cached plan when there is one."""
+        hi, lo, eps, release, _ = self._plans(req)
+        try:
+            y = np.asarray(req.y, dtype=np.float64).reshape(req.points.shape[0], -1)
+            a = np.asarray(alpha, dtype=np.float64).reshape(y.shape)
+            worst = 0.0
+            for r in range(min(columns, y.shape[1])):
+                x, info = hi.solve(y[:, r].copy(), req.eta ** 2, rtol=rtol, maxit=10 * self.maxit)
+                x = np.asarray(x)
+                worst = max(worst, float(np.linalg.norm(a[:, r] - x) / np.linalg.norm(x)))
+        finally:
+            release()
+        return worst
+
+    def serve(self, requests, load: float = 0.8, check_every: int = 0) -> dict:
+        """Serve all requests; latency statistics at `load` times the measured capacity.
+        check_every = k > 0: every k-th request's solution is also compared with the plain
+        float64 GPU solve (check_vs_fp64; outside the measured service time)."""
+        done: List[Served] = []
+        errs = []
+        for i, r in enumerate(requests):
+            alpha, rec = self.serve_one(r, keep_alpha=True)
+            done.append(rec)
+            if check_every and i % check_every == 0:
+                errs.append(self.check_vs_fp64(r, alpha))
         service = np.array([s.service_s for s in done])
         arrivals = np.array([r.arrival_s for r in requests])
         lat, rate = replay_latency(arrivals, service, load)
@@ -258,6 +418,10 @@ class Server:
             "max_relres": float(max(s.relres for s in done)),
             "max_iters": int(max(s.iters for s in done)),
             "points_total": int(sum(s.n * s.r for s in done)),
+            "cache": self.cache.stats() if self.cache is not None else None,
+            "cache_hit_rate": float(np.mean([s.cache_hit for s in done])),
+            "checked_vs_fp64": len(errs),
+            "max_rel_err_vs_fp64_gpu": float(max(errs)) if errs else None,
             "records": [s.__dict__ for s in done],
         }
 
@@ -353,16 +517,22 @@ def main():
     ap.add_argument("--slots", type=int, default=0,
                     help="requests in flight at once (continuous batching); 0 serves one at a time")
     ap.add_argument("--records", action="store_true", help="include per-request records")
+    ap.add_argument("--models", type=int, default=0,
+                    help="requests draw from this many models (points, fields, nu); 0: each its own")
+    ap.add_argument("--cache", action="store_true", help="keep each model's plans resident (PlanCache)")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="compare every k-th served solution with the plain float64 GPU solve")
     args = ap.parse_args()
     import gpinputs
     reqs = gpinputs.serving_stream(args.requests, n_min=int(args.n_min), n_max=int(args.n_max), seed=args.seed,
                                    max_rhs=args.max_rhs, dims=tuple(int(v) for v in args.dims.split(",")),
-                                   nus=tuple(float(v) for v in args.nus.split(",")))
-    srv = Server(hbm_budget=args.budget_gb * 1e9, eps_target=args.eps)
+                                   nus=tuple(float(v) for v in args.nus.split(",")), n_models=args.models)
+    srv = Server(hbm_budget=args.budget_gb * 1e9, eps_target=args.eps, cache_plans=args.cache,
+                 max_rhs=args.max_rhs)
     if args.slots > 0:
         out = srv.serve_batched(reqs, load=args.load, slots=args.slots)
     else:
-        out = srv.serve(reqs, load=args.load)
+        out = srv.serve(reqs, load=args.load, check_every=args.check_every)
         if not args.records:
             out.pop("records")
     print(json.dumps(out))

@@ -162,3 +162,70 @@ def test_levels_out_of_reach_are_skipped(abi):
     assert e.value.status == abi.GP_ENOMEM
     eps = predicted_eps(abi, req, 10 ** 13, 1e-6)
     assert eps is not None and eps > 1e-6
+
+
+class _FakePlan:
+    def __init__(self, nbytes, log, name):
+        self.info = {"bytes_resident": nbytes}
+        self.log = log
+        self.name = name
+
+    def close(self):
+        self.log.append(self.name)
+
+
+def test_plan_cache_hits_and_lru_eviction():
+    from paper_2407_03608_gb300.serving import PlanCache
+    closed = []
+    cache = PlanCache(budget=100)
+
+    def build(tag, nb=20):
+        return lambda: (_FakePlan(nb, closed, tag + "hi"), _FakePlan(nb, closed, tag + "lo"), 1e-6)
+
+    e, hit = cache.acquire("a", 40, build("a"))
+    assert not hit and cache.bytes == 40
+    cache.release(e)
+    e, hit = cache.acquire("a", 40, build("a"))
+    assert hit and cache.hits == 1 and cache.misses == 1
+    cache.release(e)
+    e_b, _ = cache.acquire("b", 40, build("b"))
+    cache.release(e_b)
+    # a third model needs room: the least recently used idle entry ("a") goes
+    e_c, hit = cache.acquire("c", 40, build("c"))
+    assert not hit and closed == ["alo", "ahi"] and set(cache.entries) == {"b", "c"}
+    # an entry in use is never evicted: hold "c", then ask for "d"; "b" goes, "c" stays
+    e_d, _ = cache.acquire("d", 40, build("d"))
+    assert "c" in cache.entries and "b" not in cache.entries
+    cache.release(e_c)
+    cache.release(e_d)
+    assert cache.stats()["evictions"] == 2
+    cache.clear()
+    assert cache.bytes == 0 and not cache.entries
+
+
+def test_plan_cache_one_user_at_a_time_and_failed_builds():
+    import threading
+    from paper_2407_03608_gb300.serving import PlanCache
+    cache = PlanCache(budget=10 ** 6)
+    log = []
+    e, _ = cache.acquire("m", 1, lambda: (_FakePlan(1, log, "h"), _FakePlan(1, log, "l"), 1e-6))
+    got = []
+
+    def second():
+        e2, hit = cache.acquire("m", 1, lambda: None)
+        got.append(hit)
+        cache.release(e2)
+
+    t = threading.Thread(target=second)
+    t.start()
+    t.join(0.2)
+    assert t.is_alive()           # waits while the first user holds the entry
+    cache.release(e)
+    t.join(5)
+    assert got == [True]
+
+    def fail():
+        raise RuntimeError("no memory")
+    with pytest.raises(RuntimeError):
+        cache.acquire("bad", 1, fail)
+    assert "bad" not in cache.entries
