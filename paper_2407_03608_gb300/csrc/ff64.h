@@ -102,6 +102,19 @@ FF_HD dd operator/(dd a, dd b) {
   return fast_two_sum(q, r / b.hi);
 }
 
+// The same sum and product without the closing FastTwoSum: the two words still add up to
+// the result, but the low word may exceed half an ulp of the high one.  The FFT passes
+// chain these inside a butterfly and renormalise each output once (renorm), which saves
+// three operations per step; a few unnormalised steps in a row cost a few u^2 of
+// accuracy, as the normalised forms do.
+FF_HD dd add_lazy(dd a, dd b) {
+  using namespace ffops;
+  const dd s = two_sum(a.hi, b.hi);
+  return {s.hi, add(s.lo, add(a.lo, b.lo))};
+}
+FF_HD dd sub_lazy(dd a, dd b) { return add_lazy(a, dd(-b.hi, -b.lo)); }
+FF_HD dd renorm(dd a) { return fast_two_sum(a.hi, a.lo); }
+
 FF_HD dd& operator+=(dd& a, dd b) { return a = a + b; }
 FF_HD dd& operator-=(dd& a, dd b) { return a = a - b; }
 FF_HD dd& operator*=(dd& a, dd b) { return a = a * b; }

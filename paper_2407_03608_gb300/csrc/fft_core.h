@@ -39,6 +39,33 @@ template <typename T>
 GPN_HD cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
 template <typename T>
 GPN_HD cpx<T> cmul(cpx<T> a, cpx<T> b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+
+// Float-float complex values inside the passes: sums without the closing renormalisation
+// (add_lazy), and a product that forms each component as TwoProd(hi, hi) - TwoProd(hi, hi)
+// with one TwoSum and the cross terms in the low word (16 operations a component instead
+// of 25 for two products and a sum).  Pass::compute renormalises its outputs once.
+GPN_HD cpx<dd> operator+(cpx<dd> a, cpx<dd> b) { return {add_lazy(a.x, b.x), add_lazy(a.y, b.y)}; }
+GPN_HD cpx<dd> operator-(cpx<dd> a, cpx<dd> b) { return {sub_lazy(a.x, b.x), sub_lazy(a.y, b.y)}; }
+// p.hi + p.lo = a b - c d (float-float, unnormalised)
+GPN_HD dd dd_dot2(dd a, dd b, dd c, dd d, float sign) {
+  using namespace ffops;
+  const float p1 = mul(a.hi, b.hi);
+  float e1 = fma(a.hi, b.hi, -p1);
+  e1 = fma(a.hi, b.lo, e1);
+  e1 = fma(a.lo, b.hi, e1);
+  const float p2 = mul(c.hi, d.hi);
+  float e2 = fma(c.hi, d.hi, -p2);
+  e2 = fma(c.hi, d.lo, e2);
+  e2 = fma(c.lo, d.hi, e2);
+  const dd s = two_sum(p1, sign * p2);
+  return {s.hi, add(s.lo, fma(sign, e2, e1))};
+}
+GPN_HD cpx<dd> cmul(cpx<dd> a, cpx<dd> b) {
+  return {dd_dot2(a.x, b.x, a.y, b.y, -1.0f), dd_dot2(a.x, b.y, a.y, b.x, 1.0f)};
+}
+template <typename T>
+GPN_HD cpx<T> renorm_c(cpx<T> a) { return a; }
+GPN_HD cpx<dd> renorm_c(cpx<dd> a) { return {renorm(a.x), renorm(a.y)}; }
 template <typename T>
 GPN_HD cpx<T> conj(cpx<T> a) { return {a.x, -a.y}; }
 // multiply by -i (forward) or +i (inverse)
@@ -108,7 +135,7 @@ GPN_HD cpx<T> w16(cpx<T> a) {
     const T cr = K == 1 ? (T)kC22 : K == 3 ? (T)kS22 : K == 5 ? -(T)kS22 : -(T)kC22;
     const T si = K == 1 ? (T)kS22 : K == 3 ? (T)kC22 : K == 5 ? (T)kC22 : (T)kS22;
     const T sn = INV ? si : -si;
-    return {a.x * cr - a.y * sn, a.x * sn + a.y * cr};
+    return cmul(a, cpx<T>{cr, sn});   // {a.x cr - a.y sn, a.x sn + a.y cr}
   }
 }
 
@@ -189,6 +216,8 @@ struct Pass {
         }
       }
       dft<INV, R>(v[b]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = renorm_c(v[b][r]);
     }
   }
 

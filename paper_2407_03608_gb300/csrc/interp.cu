@@ -18,6 +18,7 @@
 // The mbarrier wait is bounded: when it runs out the CTA records a timeout in the
 // plan's device status word and returns.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -243,24 +244,31 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
         for (int k = 0; k < CMAX; ++k)
           if (EXACT || k < ncur) red[lane * RP + k] = acc[k];
         __syncwarp();
-        double part = 0.0;
+        // w_k beta_k summed in float64, or for float-float plans in float-float (converted
+        // once at the end: float64 operations run at a small fraction of the FP32 rate)
+        using PartT = typename std::conditional<is_dd<T>::value, dd, double>::type;
+        PartT part{};
         if (grp < ppw) {   // lanes past the last full group hold no point
           for (int k = gl; k < ncur; k += Gs) {
             T sum = T(0);
             for (int row = 0; row < Gs; ++row) sum += red[(grp * Gs + row) * RP + k];
-            part += (double)((k == gl ? wk_gl : a.wk[(size_t)p * C + c0 + k]) * sum);
+            const T wkv = k == gl ? wk_gl : a.wk[(size_t)p * C + c0 + k];
+            if constexpr (is_dd<T>::value)
+              madd(part, wkv, sum);
+            else
+              part += (double)(wkv * sum);
           }
         }
         __syncwarp();   // red is rewritten by the next point batch
         for (int o = 1; o < Gs; o <<= 1) {
-          const double v = __shfl_down_sync(0xffffffffu, part, o);
+          const PartT v = shfl_down_val(part, o);
           if (gl + o < Gs) part += v;
         }
         if (active && gl == 0) {
           if (c0 == 0)
-            out_r[p] = part + shift_al;
+            out_r[p] = to_f64(part) + shift_al;
           else
-            out_r[p] += part;
+            out_r[p] += to_f64(part);
         }
         continue;
       } else if (kGroup == 32) {

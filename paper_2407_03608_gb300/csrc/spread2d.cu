@@ -258,7 +258,10 @@ constexpr int reg_channels(int C) { return C <= 16 ? C : 32; }
 
 template <typename T>
 constexpr int rows_per_warp(int nc) {
-  return (sizeof(T) == 8 || nc > 16) ? 2 : 4;
+  // float64 sums take two registers each: two rows a warp; float and float-float keep four
+  // (float-float sums are two floats, and the longer band halves the tiles a point visits,
+  // each visit evaluating its kernel values)
+  return ((sizeof(T) == 8 && !is_dd<T>::value) || nc > 16) ? 2 : 4;
 }
 
 size_t smem_bytes(size_t rs, int nc, int rpw, int w) {
@@ -321,7 +324,9 @@ void impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
 
 int spread2d_rows(const Plan& plan) {
   const int nc = reg_channels(plan.geom.C);
-  const int rpw = plan.precision == GP_FP32 ? rows_per_warp<float>(nc) : rows_per_warp<double>(nc);
+  const int rpw = plan.precision == GP_FP32   ? rows_per_warp<float>(nc)
+                  : plan.precision == GP_DF64 ? rows_per_warp<dd>(nc)
+                                              : rows_per_warp<double>(nc);
   return kWarps * rpw;
 }
 
