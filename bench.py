@@ -214,14 +214,18 @@ def launches_per_step(own_columns: bool) -> int:
     return 5 + 7 + (2 if own_columns else 0)
 
 
-# FP32 operations of the float-float arithmetic (ff64.h): add 11 (TwoSum 6, low words 2,
-# FastTwoSum 3), mul 7 (product, three fused multiply-adds, FastTwoSum 3), complex add 22,
-# complex product 50.  In-register DFTs: DFT-2 44, DFT-4 176, DFT-8 600 (two DFT-4, the
-# W8^1 and W8^3 rotations at 36 each, eight complex adds), DFT-16 1824 (two DFT-8, four
-# general W16 rotations at 50, two W8 rotations at 36, sixteen complex adds).  A radix-16
-# Stockham pass with twiddles: DFT-16 plus 15 complex products, 2574 per 16 points.
-FF_DFT = {2: 44, 4: 176, 8: 600, 16: 1824}
-FF_PASS16 = 1824 + 15 * 50
+# FP32 operations of the float-float arithmetic (ff64.h, fft_core.h) in the passes: a sum
+# without the closing renormalisation 8 (TwoSum 6, low words 2), a product 7 (product, three
+# fused multiply-adds, FastTwoSum 3), a normalised sum 11; complex: sum 16, product 34 (each
+# component two TwoProds with cross terms, a TwoSum, two closing operations), renormalisation
+# of a pass output 6.  In-register DFTs: DFT-2 32, DFT-4 128, DFT-8 456 (two DFT-4, the W8^1
+# and W8^3 rotations at 36 each, eight complex sums), DFT-16 1376 (two DFT-8, four W16
+# rotations as complex products, two W8 rotations, sixteen complex sums).  A radix-16
+# Stockham pass with twiddles: DFT-16, 15 complex products and 16 renormalisations, 1982 per
+# 16 points; a first pass at span 1 has no twiddles.
+FF_DFT = {2: 32, 4: 128, 8: 456, 16: 1376}
+FF_RENORM16 = 16 * 6
+FF_PASS16 = 1376 + 15 * 34 + FF_RENORM16
 
 
 def ff_fft_ops(L: int) -> int:
@@ -230,17 +234,18 @@ def ff_fft_ops(L: int) -> int:
     r0 = 16 if L % 4 == 0 else 1 << (L % 4)
     passes = L // 4 - (1 if L % 4 == 0 else 0)
     nt = (1 << L) // 16
-    return nt * ((16 // r0) * FF_DFT[r0] + passes * FF_PASS16)
+    return nt * ((16 // r0) * FF_DFT[r0] + FF_RENORM16 + passes * FF_PASS16)
 
 
 def alu_ops(info, R):
     """FP32 operations per launch of the float-float transform kernels, counted from their
     arithmetic (the algorithm as emulated: the bound is the FP32 issue rate).
     rows_fwd: per grid row of the data extent an nf/2-point complex FFT, then per kept mode
-      the real split (two complex adds, a complex product, two adds and two halvings: 130)
-      and the split twiddle (a complex product, shared by the RB rows of a block);
-    rows_inv: the merge of each mode pair (two merges of 116 and two twiddles of 50 per
-      pair of the nf/2 + 1 modes), then the nf/2-point FFT;
+      the real split (two complex sums, a complex product, two normalised sums and two
+      halvings: 102) and the split twiddle (a complex product, shared by the RB rows of a
+      block);
+    rows_inv: the merge of each mode pair (two merges of 88 and two twiddles of 34 per pair
+      of the nf/2 + 1 modes), then the nf/2-point FFT;
     cols_*: one nf-point complex FFT per kept mode column."""
     nf, M, W = info["nf"], info["M"], info["kernel_width"]
     C = info["n_sigma"] + 1
@@ -248,8 +253,8 @@ def alu_ops(info, R):
     ext = min(nf, int(math.ceil(nf * info["dw"] * L)) + W)
     l2 = int(round(math.log2(nf // 2)))
     rows = C * R * ext
-    fwd = rows * (ff_fft_ops(l2) + (M + 1) * 130) + C * R * (ext // 2) * (M + 1) * 50
-    inv = rows * (ff_fft_ops(l2) + (nf // 4 + 1) * 2 * (116 + 50))
+    fwd = rows * (ff_fft_ops(l2) + (M + 1) * 102) + C * R * (ext // 2) * (M + 1) * 34
+    inv = rows * (ff_fft_ops(l2) + (nf // 4 + 1) * 2 * (88 + 34))
     cols = C * R * (M + 1) * ff_fft_ops(int(round(math.log2(nf))))
     return {"rows_fwd": fwd, "rows_inv": inv, "cols_fwd": cols, "cols_inv": cols}
 
@@ -503,6 +508,20 @@ def cpu_baseline(w, gpu_out, seconds):
     return res
 
 
+def exact_rows_error(w, got, n_rows, seed):
+    """Relative l2 and largest error of `got` on seeded rows against the oracle's exact rows
+    of K alpha (direct sums over all N points, float64, host cores)."""
+    from oracle import kernel as okern
+    from oracle import rows as orows
+    orows.build()
+    wp, sig = okern.paper_fields(w.s, w.l, w.d)
+    idx = np.random.default_rng(seed).choice(w.N, size=n_rows, replace=False)
+    ref = orows.rows(w.points, wp, sig, w.nu, w.alpha, idx)
+    d = got[idx] - ref
+    return {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "rel_max": float(np.max(np.abs(d)) / np.max(np.abs(ref)))}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -673,10 +692,46 @@ def measure_serving(n_requests, n_models=12):
     return out
 
 
-def side_measurements(args, dev):
+def measure_nu_half(dev, checks, eps=5e-3):
+    """The 2-D clustered workload at nu = 1/2 on the largest grid that fits one GB300 (eps =
+    5e-3: nf = 32768, M = 6944; eps = 2.5e-3 would need nf = 65536, 560 GB in FP64): one
+    matvec of each of FP64, FP32, and both with the exact diagonal correction, timed, and
+    their outputs kept for the CPU-baseline leg to compare with exact rows of K alpha.
+    For nu = 1/2 the mode count grows like eps^-1 (Sec. 5.4), so 1e-6 is out of reach."""
+    import torch
+    import gpinputs
+    import paper_2407_03608_gb300 as gpn
+    w = gpinputs.config_2d(1_000_000, 0.5)
+    pts, s_, l_ = (torch.from_numpy(v).to(dev) for v in (w.points, w.s, w.l))
+    a = torch.from_numpy(w.alpha).to(dev)
+    out = {"workload": w.name, "eps": eps}
+    opts = None
+    for name, prec, dc in (("fp64", gpn.GP_FP64, 0), ("fp64_diag_correct", gpn.GP_FP64, 1),
+                           ("fp32", gpn.GP_FP32, 0), ("fp32_diag_correct", gpn.GP_FP32, 1)):
+        kw = dict(opts or {})
+        if dc:
+            kw["diag_correct"] = 1
+        pl = gpn.Plan(pts, s_, l_, nu=0.5, eps=eps, precision=prec, **kw)
+        if opts is None:
+            opts = {k: v for k, v in pl.matched_opts().items() if k != "diag_correct"}
+            i = pl.info
+            out.update(nf=i["nf"], M=i["M"], n_sigma=i["n_sigma"], n_t=i["n_t"], kernel_width=i["kernel_width"],
+                       transform=i["transform"])
+        pl.matvec(a)
+        ms = _events_ms(lambda: pl.matvec(a), 2)
+        res = pl.matvec(a).cpu().numpy()
+        out[name] = {"ms_per_matvec": round(ms, 3), "bytes_resident": int(pl.info["bytes_resident"])}
+        checks.append(("config2_nu_half." + name, w, res))
+        pl.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def side_measurements(args, dev, checks):
     res = {}
     for name, fn in (("config1", lambda: measure_config1(dev)),
                      ("batched", lambda: measure_batched(dev, args.n)),
+                     ("config2_nu_half", lambda: measure_nu_half(dev, checks)),
                      ("config3", lambda: measure_config3(dev)),
                      ("served", lambda: measure_serving(args.serve_requests))):
         try:
@@ -721,11 +776,21 @@ def main():
     result, w, out_sample, plan = run_ours(args, ws, rank, local)
     plan.close()
     if rank == 0:
-        if ws == 1 and not args.no_cpu_baseline:
-            result["cpu_baseline"] = cpu_baseline(w, out_sample, args.cpu_seconds)
+        checks = []
         if ws == 1 and not args.no_extras:
             import torch
-            result["side"] = side_measurements(args, torch.device("cuda", local))
+            result["side"] = side_measurements(args, torch.device("cuda", local), checks)
+        if ws == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(w, out_sample, args.cpu_seconds)
+            # the oracle's exact rows for the side measurements' outputs (this leg is the one
+            # that may run the oracle); each entry lands beside its measurement
+            for name, wk, got in checks:
+                err = exact_rows_error(wk, got, 1024, seed=31)
+                node = result["side"]
+                *path, leaf = name.split(".")
+                for key in path:
+                    node = node.setdefault(key, {})
+                node.setdefault(leaf, {})["rel_err_vs_1024_exact_rows"] = err
         print(json.dumps(result), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -87,3 +87,36 @@ def test_three_dimensional_workload(gpn):
         p32.close()
     e_rows = _rows_error(w, got, 256, seed=32)
     assert e_rows <= 1e-4, e_rows
+
+
+def test_nu_half_on_the_largest_grid(gpn):
+    """Config 2 at nu = 1/2: the largest grid that fits (eps = 5e-3, nf = 32768; the mode count
+    grows like eps^-1, Sec. 5.4) in FP64 and FP32, with and without the exact diagonal
+    correction, against 1024 exact rows of K alpha.  The FP64 error meets the eps the plan was
+    built for, FP32 adds no more than 1e-5 to it, and the diagonal correction does not make
+    it worse."""
+    if _free_after_cleanup() < 150e9:
+        pytest.skip("needs about 141 GB of free device memory")
+    w = gpinputs.config_2d(1_000_000, 0.5)
+    a = torch.from_numpy(w.alpha).cuda()
+    errs = {}
+    opts = None
+    for name, prec, dc in (("fp64", gpn.GP_FP64, 0), ("fp64_dc", gpn.GP_FP64, 1), ("fp32", gpn.GP_FP32, 0),
+                           ("fp32_dc", gpn.GP_FP32, 1)):
+        kw = dict(opts or {})
+        if dc:
+            kw["diag_correct"] = 1
+        w.eps = 5e-3
+        p = _plan(gpn, w, prec, **kw)
+        try:
+            if opts is None:
+                assert p.info["nf"] == 32768
+                opts = {k: v for k, v in p.matched_opts().items() if k != "diag_correct"}
+            got = p.matvec(a).cpu().numpy()
+        finally:
+            p.close()
+        _free_after_cleanup()
+        errs[name] = _rows_error(w, got, 1024, seed=31)
+    assert errs["fp64"] <= 5e-3, errs
+    assert abs(errs["fp32"] - errs["fp64"]) <= 1e-5, errs
+    assert errs["fp64_dc"] <= 1.05 * errs["fp64"] and errs["fp32_dc"] <= 1.05 * errs["fp32"], errs
