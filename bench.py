@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--profile-case", action="store_true",
                     help="a fixed workload for profilers: build one plan (--d, --n, --eps, --precision, "
                          "--transform) and run --matvecs matvecs, nothing else")
+    ap.add_argument("--solve-compare", action="store_true",
+                    help="time to solution on the benchmark workload: plain float64-grade CG against the "
+                         "refined FP32 solve, both to --rtol, and the difference of the two solutions")
+    ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--d", type=int, default=2, choices=[2, 3])
     ap.add_argument("--matvecs", type=int, default=4)
     ap.add_argument("--transform", type=int, default=0)
@@ -764,11 +768,62 @@ def run_profile_case(args):
     plan.close()
 
 
+def run_solve_compare(args):
+    """Time to solution on the 2-D workload (N = 1e6, Matern 3/2, eps = 1e-6): plain CG on the
+    float64-grade plan (float-float, one right-hand side, no refinement) against the refined
+    solve (FP32 inner CG to 1e-4 per refinement step, residuals on the float-float plan),
+    both to relative residual --rtol; wall time of each solve (synchronised), iterations, and
+    the relative difference of the two solutions.  The native float64 path is timed over 20
+    iterations and its time to solution extrapolated to the plain CG's iteration count
+    (labelled as such)."""
+    import torch
+    import paper_2407_03608_gb300 as gpn
+    from paper_2407_03608_gb300 import abi
+    dev = torch.device("cuda", 0)
+    w = workload(args)
+    pts, s_, l_, y = (torch.from_numpy(v).to(dev) for v in (w.points, w.s, w.l, w.y))
+    eta2 = w.eta ** 2
+    hi = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_DF64)
+    lo = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, **hi.matched_opts())
+    out = {"workload": w.name, "rtol": args.rtol}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    (xr, ir), t_ref = timed(lambda: hi.solve_refined(lo, y, eta2, rtol=args.rtol, maxit=200000, outer_max=30))
+    out["refined_fp32_inner"] = {"seconds": round(t_ref, 3), "inner_iters": int(ir["iters"][0]),
+                                 "relres": float(ir["relres"][0]), "status": int(ir["status"])}
+    (xp, ip), t_plain = timed(lambda: hi.solve(y, eta2, rtol=args.rtol, maxit=200000))
+    out["plain_cg_df64"] = {"seconds": round(t_plain, 3), "iters": int(ip["iters"][0]),
+                            "relres": float(ip["relres"][0]), "status": int(ip["status"])}
+    d = xr - xp
+    out["refined_vs_plain"] = {"rel_l2": float(torch.linalg.norm(d) / torch.linalg.norm(xp)),
+                               "rel_max": float(d.abs().max() / xp.abs().max())}
+    lo.close()
+    p64 = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP64, **hi.matched_opts())
+    x64 = torch.empty_like(y)
+    abi.gp_cg_solve(p64.handle, y, x64, 1, eta2, 1e-30, 2)
+    ms = _events_ms(lambda: abi.gp_cg_solve(p64.handle, y, x64, 1, eta2, 1e-30, 20), 1) / 20
+    out["plain_cg_fp64_extrapolated"] = {"ms_per_iter": round(ms, 3),
+                                         "seconds": round(ms * 1e-3 * out["plain_cg_df64"]["iters"], 1),
+                                         "note": "20 iterations timed, times the float-float CG's iteration count"}
+    p64.close()
+    hi.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.solve_compare:
+        run_solve_compare(args)
         return
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -349,6 +349,17 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   const int C = h.n_sigma + 1;
   ps.C = C;
   h.tile = (o.set & GP_SET_TILE) ? o.tile : choose_tile(d, C, rs, h.width);
+  if (!(o.set & GP_SET_TILE) && o.precision == GP_DF64 && d == 2) {
+    // float-float plans spread with the register kernel (its tiles do not depend on this
+    // edge), so the edge sizes the interpolation's staged blocks and the spread's candidate
+    // bins: 24 cells measured best (22.9 ms a CG iteration on the 2-D benchmark workload,
+    // against 23.7 at 16 and 25.2 at 32)
+    for (int t : {24, 16, 32, 12, 8})
+      if (tile_ok(d, t, C, rs, h.width, kSpreadSmemMax) || tile_ok(d, t, 1, rs, h.width, kSpreadSmemMax)) {
+        h.tile = t;
+        break;
+      }
+  }
   GPN_CHECK(d == 1 || (h.tile * rs) % 16 == 0, GP_EINVAL,
             "tile must be a multiple of 16 bytes of grid values (4 in FP32, 2 in FP64) for d >= 2");
   GPN_CHECK(h.tile >= h.width - 1 && h.tile >= 1, GP_EINVAL, "tile must be >= kernel width - 1");

@@ -83,6 +83,12 @@ __device__ __forceinline__ void load_rb(const cpx<T>* o, cpx<T> (&v)[RB]) {
   }
 }
 
+// Radix-16 passes are unrolled for float and double; float-float passes run as a loop (a
+// float-float pass is about 2000 instructions a thread, and unrolled passes overflow the
+// instruction cache)
+template <typename T>
+constexpr int kPassUnroll = is_dd<T>::value ? 1 : 4;
+
 // shared-memory elements of one row buffer: the padded length-N2 FFT plus the slot N2,
 // rounded up to an even count (16-byte alignment of what follows)
 __host__ __device__ constexpr int row_buf(int n2) { return (n2 + n2 / 16 + 2) & ~1; }
@@ -143,7 +149,7 @@ __device__ __forceinline__ void fft_block_from_regs(cpx<T>* b, const cpx<T> (&x)
   }
   __syncthreads();
   int Ns = R0;
-#pragma unroll
+#pragma unroll (kPassUnroll<T>)
   for (int s = (L % 4 == 0) ? 1 : 0; s < L / 4; ++s) {
     fft::Pass<16, 1, T> p;
     p.load(b, N, t, NT);
@@ -176,7 +182,7 @@ __device__ __forceinline__ void fft_block_to(cpx<T>* b, const fft::Twiddle2<T>& 
     __syncthreads();
     Ns *= R;
   }
-#pragma unroll
+#pragma unroll (kPassUnroll<T>)
   for (int s = 0; s < L / 4; ++s) {
     fft::Pass<16, 1, T> p;
     p.load(b, N, t, NT);
@@ -409,7 +415,7 @@ __device__ __forceinline__ void fft_block_regs_to(cpx<T>* b, const cpx<T> (&x)[1
   }
   __syncthreads();
   int Ns = R0;
-#pragma unroll
+#pragma unroll (kPassUnroll<T>)
   for (int s = 0; s < S; ++s) {
     fft::Pass<16, 1, T> p;
     p.load(b, N, t, NT);

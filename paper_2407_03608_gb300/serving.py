@@ -39,7 +39,7 @@ from typing import List, Optional
 
 import numpy as np
 
-EPS_LADDER = (1e-6, 1e-5, 1e-4, 1e-3)
+EPS_LADDER = (1e-6, 1e-5, 1e-4, 1e-3, 1e-2)
 
 
 @dataclass
@@ -57,6 +57,7 @@ class Served:
     relres: float
     bytes_resident: int
     cache_hit: bool = False
+    rejected: bool = False     # no eps level of the ladder fits the budget (nothing solved)
 
 
 def _rhs(req) -> int:
@@ -64,9 +65,10 @@ def _rhs(req) -> int:
     return 1 if y.ndim == 1 else int(y.shape[1])
 
 
-def predicted_footprint(abi, req, eps: float) -> int:
+def predicted_footprint(abi, req, eps: float, max_rhs: Optional[int] = None, rhs_block: int = 0) -> int:
     """Device bytes of the request's FP64 and FP32 plans at `eps`, predicted on the host
-    (gp_plan_params, no allocation)."""
+    (gp_plan_params, no allocation); max_rhs (default: the request's R) and rhs_block as
+    the plans will be built."""
     x = np.asarray(req.points, dtype=np.float64)
     N, d = x.shape
     l = np.asarray(req.l, dtype=np.float64)                      # the plan's fields are (s, l)
@@ -74,19 +76,21 @@ def predicted_footprint(abi, req, eps: float) -> int:
     total = 0
     for prec in (abi.GP_FP64, abi.GP_FP32):
         info = abi.gp_plan_params(d, N, req.nu, eps, float(l.min()), float(l.max()), lo, hi,
-                                  abi.default_opts(precision=prec, max_rhs=_rhs(req)))
+                                  abi.default_opts(precision=prec, max_rhs=max_rhs or _rhs(req),
+                                                   rhs_block=rhs_block))
         total += int(info["bytes_resident"])
     return total
 
 
-def predicted_eps(abi, req, budget: int, eps_target: float) -> Optional[float]:
+def predicted_eps(abi, req, budget: int, eps_target: float, max_rhs: Optional[int] = None,
+                  rhs_block: int = 0) -> Optional[float]:
     """The finest eps of the ladder (from eps_target) at which the request's FP64 and FP32
     plans together are predicted to fit `budget` bytes.  None when even the coarsest level
     does not fit.  A level whose parameters are out of reach (gp_plan_params reports
     GP_ENOMEM or GP_EUNSUPPORTED, as for nu = 1/2 at tight eps) does not fit."""
     for eps in [e for e in EPS_LADDER if e >= eps_target * (1 - 1e-12)]:
         try:
-            need = predicted_footprint(abi, req, eps)
+            need = predicted_footprint(abi, req, eps, max_rhs, rhs_block)
         except abi.GPError as e:
             if e.status in (abi.GP_ENOMEM, abi.GP_EUNSUPPORTED):
                 continue
@@ -222,7 +226,7 @@ class Server:
 
     def __init__(self, hbm_budget: float = 120e9, eps_target: float = 1e-6, rtol: float = 1e-8,
                  inner_rtol: float = 1e-4, maxit: int = 20000, outer_max: int = 20, cache_plans: bool = False,
-                 max_rhs: int = 16, rhs_block: int = 4):
+                 max_rhs: int = 16, rhs_block: int = 1):
         import paper_2407_03608_gb300 as gpn
         self.gpn = gpn
         self.budget = int(hbm_budget)
@@ -231,7 +235,9 @@ class Server:
         self.inner_rtol = inner_rtol
         self.maxit = maxit
         self.outer_max = outer_max
-        # cached plans take any request on their model: max_rhs columns, grids for rhs_block
+        # cached plans take any request on their model: max_rhs columns through grids held for
+        # rhs_block of them (one by default: the columns share every CG iteration, and a
+        # three-dimensional grid set can take tens of GB)
         self.cache = PlanCache(self.budget) if cache_plans else None
         self.max_rhs = max_rhs
         self.rhs_block = rhs_block
@@ -243,7 +249,7 @@ class Server:
         extra = {} if stream_handle is None else {"stream": stream_handle}
         if self.cache is not None:
             extra.update(max_rhs_override=self.max_rhs, rhs_block=min(self.rhs_block, self.max_rhs))
-        start = predicted_eps(gpn.abi, req, self.budget, self.eps_target) or EPS_LADDER[-1]
+        start = predicted_eps(gpn.abi, req, self.budget, self.eps_target, *self._sizes(req)) or EPS_LADDER[-1]
         hi, eps = _plan_fitting(gpn, req, self.budget // 2, max(start, self.eps_target), gpn.GP_FP64, extra=extra)
         try:
             kw = dict(extra)
@@ -255,6 +261,16 @@ class Server:
             raise
         return hi, lo, eps
 
+    def _rejected(self, req, seconds):
+        return Served(req.rid, req.points.shape[0], req.points.shape[1], req.nu, _rhs(req), None, seconds, seconds,
+                      0.0, 0, 0.0, 0, False, True)
+
+    def _sizes(self, req):
+        """(max_rhs, rhs_block) the request's plans are built with."""
+        if self.cache is None:
+            return _rhs(req), 0
+        return self.max_rhs, min(self.rhs_block, self.max_rhs)
+
     def _plans(self, req, stream_handle=None):
         """(hi, lo, eps, release, hit): the request's plans, from the cache when it has them."""
         if self.cache is None:
@@ -265,8 +281,8 @@ class Server:
                 hi.close()
             return hi, lo, eps, release, False
         key = (req.model if req.model >= 0 else -1 - req.rid, self.eps_target)
-        eps0 = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target)
-        need = self.budget if eps0 is None else predicted_footprint(self.gpn.abi, req, eps0)
+        eps0 = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target, *self._sizes(req))
+        need = self.budget if eps0 is None else predicted_footprint(self.gpn.abi, req, eps0, *self._sizes(req))
         entry, hit = self.cache.acquire(key, need, lambda: self._build_pair(req, stream_handle))
         hi, lo, eps = entry.plans
         return hi, lo, eps, (lambda: self.cache.release(entry)), hit
@@ -278,7 +294,13 @@ class Server:
         # admission by the host-side footprint prediction; building at that level can still
         # run out of memory, so the ladder continues from there (or the model's plans are
         # already resident)
-        hi, lo, eps, release, hit = self._plans(req)
+        try:
+            hi, lo, eps, release, hit = self._plans(req)
+        except self.gpn.GPError as e:
+            if e.status not in (self.gpn.abi.GP_ENOMEM, self.gpn.abi.GP_EUNSUPPORTED):
+                raise
+            rec = self._rejected(req, time.perf_counter() - t0)
+            return (None, rec) if keep_alpha else rec
         try:
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -302,7 +324,12 @@ class Server:
         FP32 plans at the admitted eps, then the refined solve.  Returns (alpha, Served)."""
         sh = stream.cuda_stream
         t0 = time.perf_counter()
-        hi, lo, eps, release, hit = self._plans(req, sh)
+        try:
+            hi, lo, eps, release, hit = self._plans(req, sh)
+        except self.gpn.GPError as e:
+            if e.status not in (self.gpn.abi.GP_ENOMEM, self.gpn.abi.GP_EUNSUPPORTED):
+                raise
+            return None, self._rejected(req, time.perf_counter() - t0)
         try:
             stream.synchronize()
             t1 = time.perf_counter()
@@ -331,9 +358,10 @@ class Server:
         arr = np.zeros(len(requests)) if arrivals is None else np.asarray(arrivals, dtype=np.float64)
         need = []
         for req in requests:
-            eps = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target)
+            eps = predicted_eps(self.gpn.abi, req, self.budget, self.eps_target, *self._sizes(req))
             # a request that fits no level is admitted alone (it holds the whole budget)
-            need.append(self.budget if eps is None else predicted_footprint(self.gpn.abi, req, eps))
+            need.append(self.budget if eps is None else predicted_footprint(self.gpn.abi, req, eps,
+                                                                            *self._sizes(req)))
         device = torch.cuda.current_device()
 
         def make_stream():
@@ -356,8 +384,11 @@ class Server:
         rate = load * capacity
         rel = (arr - arr[0]) * (rate0 / rate)
         res, info = self.serve_concurrent(requests, slots=slots, arrivals=rel)
-        lat = np.array([r[3] - rel[i] for i, r in enumerate(res)])
-        service = np.array([r[3] - r[2] for r in res])
+        keep = [i for i, r in enumerate(res) if not r[1].rejected]
+        lat = np.array([res[i][3] - rel[i] for i in keep])
+        service = np.array([res[i][3] - res[i][2] for i in keep])
+        rejected = len(res) - len(keep)
+        res = [res[i] for i in keep]
         return {
             "slots": slots,
             "requests": len(res),
@@ -369,6 +400,7 @@ class Server:
             "service_p50_s": float(np.percentile(service, 50)),
             "service_p99_s": float(np.percentile(service, 99)),
             "max_in_flight": int(info["max_inflight"]),
+            "rejected": rejected,
             "max_relres": float(max(r[1].relres for r in res)),
             "cache_hit_rate": float(np.mean([r[1].cache_hit for r in res])),
         }
@@ -399,8 +431,11 @@ class Server:
         for i, r in enumerate(requests):
             alpha, rec = self.serve_one(r, keep_alpha=True)
             done.append(rec)
-            if check_every and i % check_every == 0:
+            if check_every and i % check_every == 0 and not rec.rejected:
                 errs.append(self.check_vs_fp64(r, alpha))
+        rejected = [s for s in done if s.rejected]
+        done = [s for s in done if not s.rejected]
+        requests = [r for r in requests if r.rid not in {s.rid for s in rejected}]
         service = np.array([s.service_s for s in done])
         arrivals = np.array([r.arrival_s for r in requests])
         lat, rate = replay_latency(arrivals, service, load)
@@ -418,6 +453,7 @@ class Server:
             "max_relres": float(max(s.relres for s in done)),
             "max_iters": int(max(s.iters for s in done)),
             "points_total": int(sum(s.n * s.r for s in done)),
+            "rejected": len(rejected),
             "cache": self.cache.stats() if self.cache is not None else None,
             "cache_hit_rate": float(np.mean([s.cache_hit for s in done])),
             "checked_vs_fp64": len(errs),
