@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the side measurements (config 1 latency, batched R, config 3, served solves)")
-    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true",
                     help="a fixed workload for profilers: build one plan (--d, --n, --eps, --precision, "
                          "--transform) and run --matvecs matvecs, nothing else")
@@ -248,8 +248,9 @@ def alu_ops(info, R):
       the real split (two complex sums, a complex product, two normalised sums and two
       halvings: 102) and the split twiddle (a complex product, shared by the RB rows of a
       block);
-    rows_inv: the merge of each mode pair (two merges of 88 and two twiddles of 34 per pair
-      of the nf/2 + 1 modes), then the nf/2-point FFT;
+    rows_inv: the merge of each mode pair (two merges of 88 and one twiddle of 34 per pair
+      of the nf/2 + 1 modes: the second twiddle is minus the conjugate of the first), then
+      the nf/2-point FFT;
     cols_*: one nf-point complex FFT per kept mode column."""
     nf, M, W = info["nf"], info["M"], info["kernel_width"]
     C = info["n_sigma"] + 1
@@ -258,7 +259,7 @@ def alu_ops(info, R):
     l2 = int(round(math.log2(nf // 2)))
     rows = C * R * ext
     fwd = rows * (ff_fft_ops(l2) + (M + 1) * 102) + C * R * (ext // 2) * (M + 1) * 34
-    inv = rows * (ff_fft_ops(l2) + (nf // 4 + 1) * 2 * (88 + 34))
+    inv = rows * (ff_fft_ops(l2) + (nf // 4 + 1) * (2 * 88 + 34))
     cols = C * R * (M + 1) * ff_fft_ops(int(round(math.log2(nf))))
     return {"rows_fwd": fwd, "rows_inv": inv, "cols_fwd": cols, "cols_inv": cols}
 
@@ -670,7 +671,7 @@ def measure_config3(dev, steps=3):
                                   "bytes_resident": lean_bytes}}
 
 
-def measure_serving(n_requests, n_models=12):
+def measure_serving(n_requests, n_models=8):
     """A bounded sample of the serving stream: requests on `n_models` models (points, fields,
     nu; popularity 1/k), solved to rtol 1e-8 (FP32 CG inside float64 refinement) with each
     model's plans kept resident (PlanCache, 120 GB budget); p50/p99 latency at 80% of the
@@ -678,7 +679,7 @@ def measure_serving(n_requests, n_models=12):
     10th served solution compared with the plain float64 GPU solve."""
     import gpinputs
     from paper_2407_03608_gb300.serving import Server
-    reqs = gpinputs.serving_stream(n_requests, n_min=1000, n_max=20_000, dims=(1, 2, 3), nus=(0.5, 1.5, 2.5),
+    reqs = gpinputs.serving_stream(n_requests, n_min=1000, n_max=20_000, dims=(1, 2), nus=(0.5, 1.5, 2.5),
                                    max_rhs=16, n_models=n_models)
     srv = Server(hbm_budget=120e9, eps_target=1e-6, cache_plans=True)
     out = srv.serve(reqs, load=0.8, check_every=10)
@@ -692,7 +693,8 @@ def measure_serving(n_requests, n_models=12):
     out["continuous_batching"] = srv.serve_batched(reqs, load=0.8, slots=3)
     srv.cache.clear()
     out["sample"] = ("%d requests of the serving stream (seed 100) on %d models: N log-uniform in [1e3, 2e4], "
-                     "d in {1, 2, 3}, nu in {1/2, 3/2, 5/2}, R in 1..16" % (n_requests, n_models))
+                     "d in {1, 2}, nu in {1/2, 3/2, 5/2}, R in 1..16 (3-D models: a separate run, their grids "
+                     "cost seconds an iteration)" % (n_requests, n_models))
     return out
 
 

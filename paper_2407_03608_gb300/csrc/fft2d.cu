@@ -11,12 +11,13 @@
 //      plus the real split (fft_core.h).  The CTA keeps the modes m = 0..M and writes
 //      X[cr][m][y] (cr = rhs * C + channel), the RB rows side by side.  Rows outside
 //      [row_lo, row_hi) are never written and stay zero.
-//   2. columns, forward: cuFFT, batched 1-D C2C of length nf over the C R (M+1)
-//      contiguous columns, from X into Y.
+//   2. columns, forward: batched 1-D C2C of length nf over the C R (M+1) contiguous
+//      columns, from X into Y: cuFFT for float and double plans, the library's own
+//      k_cols for float-float plans (cuFFT has no float-float type).
 //   3. step 3 (k_diag_t): a_k = sum_l A'_kl b_l for |n_1| <= M, from Y into Z.  A'
 //      depends on |n_1| and m only; one thread serves n_1 and -n_1 from the same A'
 //      entries.  Rows |n_1| > M of Z stay zero from plan creation on.
-//   4. columns, inverse: cuFFT, from Z into Y.
+//   4. columns, inverse: cuFFT or k_cols, from Z into Y.
 //   5. rows, inverse (k_rows_inv): each CTA reads the modes 0..M of RB rows, merges
 //      them into the nf/2-point complex input, runs the inverse FFT and writes the
 //      columns [col_lo, col_hi) of the grid rows.
@@ -83,11 +84,10 @@ __device__ __forceinline__ void load_rb(const cpx<T>* o, cpx<T> (&v)[RB]) {
   }
 }
 
-// Radix-16 passes are unrolled for float and double; float-float passes run as a loop (a
-// float-float pass is about 2000 instructions a thread, and unrolled passes overflow the
-// instruction cache)
+// Radix-16 passes are unrolled (measured: running the float-float passes as a loop, to
+// shrink the code, made the column kernels 27 % slower)
 template <typename T>
-constexpr int kPassUnroll = is_dd<T>::value ? 1 : 4;
+constexpr int kPassUnroll = 4;
 
 // shared-memory elements of one row buffer: the padded length-N2 FFT plus the slot N2,
 // rounded up to an even count (16-byte alignment of what follows)
@@ -342,8 +342,10 @@ __global__ void __launch_bounds__(RB*(1 << L) / 16, (rows_min_blocks<T, L, RB>()
       const int r = kk / H, k = kk - r * H;
       cpx<T>* br = buf + r * BUF;
       const cpx<T> xk = br[fft::pad(k)], xn = br[fft::pad(N2 - k)];
-      const cpx<T> zk = fft::c2r_merge(xk, xn, wn(k));
-      if (k != 0 && k != N2 / 2) br[fft::pad(N2 - k)] = fft::c2r_merge(xn, xk, wn(N2 - k));
+      // W_nf^(N2 - k) = W_nf^(N2) W_nf^(-k) = -conj(W_nf^k): one twiddle serves the pair
+      const cpx<T> w = wn(k);
+      const cpx<T> zk = fft::c2r_merge(xk, xn, w);
+      if (k != 0 && k != N2 / 2) br[fft::pad(N2 - k)] = fft::c2r_merge(xn, xk, cpx<T>{-w.x, w.y});
       br[fft::pad(k)] = zk;
     }
     __syncthreads();
