@@ -799,6 +799,7 @@ def run_solve_compare(args):
     (xr, ir), t_ref = timed(lambda: hi.solve_refined(lo, y, eta2, rtol=args.rtol, maxit=200000, outer_max=30))
     out["refined_fp32_inner"] = {"seconds": round(t_ref, 3), "inner_iters": int(ir["iters"][0]),
                                  "relres": float(ir["relres"][0]), "status": int(ir["status"])}
+    print(json.dumps(out), file=sys.stderr, flush=True)   # progress: the refined solve alone
     (xp, ip), t_plain = timed(lambda: hi.solve(y, eta2, rtol=args.rtol, maxit=200000))
     out["plain_cg_df64"] = {"seconds": round(t_plain, 3), "iters": int(ip["iters"][0]),
                             "relres": float(ip["relres"][0]), "status": int(ip["status"])}
