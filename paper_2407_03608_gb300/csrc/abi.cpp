@@ -406,7 +406,8 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   const long long spectra = (ps.tr3 || ps.rowfft) ? 3 * (d == 2 ? h.nf : 1) * CR * (h.M + 1) * 2 * (long long)rs
                                                   : CR * S * 2 * (long long)rs;
   ps.est_rest = 2 * CR * G * (long long)rs + spectra + N * (long long)(d * (4 + rs) + 8 + C * rs) +
-                (long long)N * max_rhs * 8 * 9;
+                (long long)N * max_rhs * 8 * 9 +
+                (psi_tabulated(d, o.precision) ? N * (long long)d * h.width * (long long)rs : 0);
   // step 3: the stored tensor A' (1) or the memory-lean form from per-dimension
   // factors (2); auto takes the tensor unless it alone breaks max_bytes or the free
   // device memory

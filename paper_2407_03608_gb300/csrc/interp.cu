@@ -32,6 +32,7 @@ template <typename T>
 struct InterpArgs {
   const int* cell0[kMaxDim];
   const T* xi[kMaxDim];
+  const T* psi[kMaxDim];   // tabulated kernel values [n][width] per axis (null: evaluate)
   const T* wk;
   const int* bin_start;
   const int* bins;       // non-empty bins
@@ -207,7 +208,9 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
         const int src = kGroup == 0 ? grp * Gs : 0;
         T pq[kMaxDim];
 #pragma unroll
-        for (int q = 0; q < D; ++q) pq[q] = gl < W ? psi_at<T>(gl, x[q], a.beta, a.inv_halfw) : T(0);
+        for (int q = 0; q < D; ++q)
+          pq[q] = gl < W ? (a.psi[q] ? a.psi[q][(size_t)p * W + gl] : psi_at<T>(gl, x[q], a.beta, a.inv_halfw))
+                         : T(0);
         for (int pen0 = 0; pen0 < P; pen0 += Gs) {
           const int pen = pen0 + gl;
           const bool valid = active && pen < P;
@@ -343,6 +346,7 @@ void interp_impl(Plan& plan, const PointSet& ps, const double* alpha_sorted, dou
   for (int q = 0; q < kMaxDim; ++q) {
     a.cell0[q] = ps.cell0[q];
     a.xi[q] = (const T*)ps.xi[q];
+    a.psi[q] = (const T*)ps.psi[q];
     a.nbins[q] = ps.nbins[q];
   }
   a.wk = (const T*)ps.wk;

@@ -28,6 +28,10 @@ struct PointSet {
   int* bin_start = nullptr;                            // nbins_total + 1 offsets
   int* active_bins = nullptr;                          // bins holding at least one point
   long long n_active_bins = 0;
+  // kernel values psi(j - xi_a), j < width, per axis [n][width] (real_t, sorted order):
+  // tabulated once for the 2-D float64 and float-float plans, whose kernel values cost
+  // a float64 or float-float exponential each; null otherwise (the kernels evaluate psi)
+  void* psi[kMaxDim] = {nullptr, nullptr, nullptr};
 };
 
 // Launch parameters shared by the kernels.
@@ -151,6 +155,10 @@ struct Plan {
   cufftHandle fwd_plan(int R);
   cufftHandle inv_plan(int R);
 };
+
+// Kernel values tabulated per point (PointSet::psi): the 2-D float64 and float-float plans
+inline bool psi_tabulated(int d, int precision) { return d == 2 && precision != GP_FP32; }
+inline bool psi_tabulated(const Plan& p) { return psi_tabulated(p.geom.d, p.precision); }
 
 // Hyperparameters, layout and device footprint of a plan (host only; abi.cpp).
 struct PlanShape {

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "ff64.h"
+#include "kernels.h"
 #include "plan.h"
 
 namespace gpn {
@@ -198,7 +199,19 @@ __global__ void k_gather_points(const int* __restrict__ perm, long long n, int d
   wabs[p] = (float)m;
 }
 
-inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+// psi(j - xi_a(p)) for every sorted point p, axis a < d and j < W (the values the spread and
+// the interpolation would otherwise evaluate at every visit of the point)
+template <typename T>
+__global__ void k_psi_tables(long long n, int d, int W, const T* __restrict__ x0, const T* __restrict__ x1,
+                             const T* __restrict__ x2, T beta, T inv_halfw, T* t0, T* t1, T* t2) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n * W) return;
+  const long long p = i / W;
+  const int j = (int)(i - p * W);
+  const T* xs[3] = {x0, x1, x2};
+  T* ts[3] = {t0, t1, t2};
+  for (int a = 0; a < d; ++a) ts[a][i] = psi_at<T>(j, xs[a][p], beta, inv_halfw);
+}
 
 // dst[p + r N] = src[perm[p] + r N]
 __global__ void k_gather(const int* __restrict__ perm, const double* __restrict__ src, double* __restrict__ dst,
@@ -354,6 +367,20 @@ void build_pointset(Plan& plan, PointSet& ps, const double* x_dev, const double*
             (double*)ps.xi[1], (double*)ps.xi[2], w_dev, sig_dev, cb, (double*)ps.wk, ps.wabs);
     }
     chk(cudaGetLastError());
+    if (n > 0 && psi_tabulated(plan) && e == cudaSuccess) {
+      const int W = h.width;
+      for (int a = 0; a < d; ++a) ps.psi[a] = alloc(actx, rs * nn * W);
+      if (plan.precision == GP_DF64)
+        k_psi_tables<dd><<<blocks_for(n * W, 256), 256, 0, st>>>(
+            n, d, W, (const dd*)ps.xi[0], (const dd*)ps.xi[1], (const dd*)ps.xi[2], es_beta_arg<dd>(h.beta),
+            dd(2.0 / h.width), (dd*)ps.psi[0], (dd*)ps.psi[1], (dd*)ps.psi[2]);
+      else
+        k_psi_tables<double><<<blocks_for(n * W, 256), 256, 0, st>>>(
+            n, d, W, (const double*)ps.xi[0], (const double*)ps.xi[1], (const double*)ps.xi[2],
+            es_beta_arg<double>(h.beta), 2.0 / h.width, (double*)ps.psi[0], (double*)ps.psi[1],
+            (double*)ps.psi[2]);
+      chk(cudaGetLastError());
+    }
     chk(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st));
     chk(cudaStreamSynchronize(st));
   }

@@ -52,6 +52,8 @@ struct Spread2Args {
   const T* xiy;
   const T* xix;
   const T* wk;           // [n][C]
+  const T* psy;          // tabulated kernel values [n][width] per axis (null: evaluate)
+  const T* psx;
   const int* bin_start;
   const int* tiles;      // active tile ids, ty * ntx + tx
   int ntx;
@@ -182,10 +184,20 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
       const T yq = a.xiy[p], xq = a.xix[p];
       T* py = s_psy + slot * SY;
       T* px = s_psx + slot * PSX;
-      for (int j = 0; j < W; ++j) px[j] = psi_at<T>(j, xq, a.beta, a.inv_halfw);
-      for (int j = 0; j < SY; ++j) {
-        const int jj = j - (RPW - 1);
-        py[j] = (jj >= 0 && jj < W) ? psi_at<T>(jj, yq, a.beta, a.inv_halfw) : T(0);
+      if (a.psx) {
+        const T* tx = a.psx + (size_t)p * W;
+        const T* ty = a.psy + (size_t)p * W;
+        for (int j = 0; j < W; ++j) px[j] = tx[j];
+        for (int j = 0; j < SY; ++j) {
+          const int jj = j - (RPW - 1);
+          py[j] = (jj >= 0 && jj < W) ? ty[jj] : T(0);
+        }
+      } else {
+        for (int j = 0; j < W; ++j) px[j] = psi_at<T>(j, xq, a.beta, a.inv_halfw);
+        for (int j = 0; j < SY; ++j) {
+          const int jj = j - (RPW - 1);
+          py[j] = (jj >= 0 && jj < W) ? psi_at<T>(jj, yq, a.beta, a.inv_halfw) : T(0);
+        }
       }
       const T amp = (T)alpha_r[p];
       const T* wkp = a.wk + (size_t)p * C;
@@ -299,6 +311,8 @@ void impl(Plan& plan, const double* alpha_sorted, int R, cudaStream_t st) {
   a.l0x = ps.cell0[1];
   a.xiy = (const T*)ps.xi[0];
   a.xix = (const T*)ps.xi[1];
+  a.psy = (const T*)ps.psi[0];
+  a.psx = (const T*)ps.psi[1];
   a.wk = (const T*)ps.wk;
   a.bin_start = ps.bin_start;
   a.tiles = plan.sp2_tiles;
