@@ -551,13 +551,13 @@ __global__ void __launch_bounds__(128) k_diag_t(DiagTArgs<T> a) {
         for (int l = 0; l < NC; ++l) {
           const int lo = k < l ? k : l, hi = k < l ? l : k;
           const T w = av[lo * NC - lo * (lo - 1) / 2 + (hi - lo)];
-          madd(ap.x, w, bp[l].x);
-          madd(ap.y, w, bp[l].y);
-          madd(an.x, w, bn[l].x);
-          madd(an.y, w, bn[l].y);
+          madd_lazy(ap.x, w, bp[l].x);
+          madd_lazy(ap.y, w, bp[l].y);
+          madd_lazy(an.x, w, bn[l].x);
+          madd_lazy(an.y, w, bn[l].y);
         }
-        Zr[k * colstride + off_p] = ap;
-        if (n1 != 0) Zr[k * colstride + off_n] = an;
+        Zr[k * colstride + off_p] = {renorm_val(ap.x), renorm_val(ap.y)};
+        if (n1 != 0) Zr[k * colstride + off_n] = {renorm_val(an.x), renorm_val(an.y)};
       }
     }
     return;

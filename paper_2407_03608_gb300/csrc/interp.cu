@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
             const T wgt = psi_at<T>(i, x[0], a.beta, a.inv_halfw);
 #pragma unroll
             for (int k = 0; k < CMAX; ++k)
-              if (EXACT || k < ncur) madd(acc[k], wgt, rowp[(size_t)k * SV + i]);
+              if (EXACT || k < ncur) madd_lazy(acc[k], wgt, rowp[(size_t)k * SV + i]);
           }
         }
       } else {
@@ -234,11 +234,14 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs<T> a, const __grid_co
             if (valid) {
 #pragma unroll
               for (int k = 0; k < CMAX; ++k)
-                if (EXACT || k < ncur) madd(acc[k], wgt, rowp[(size_t)k * SV + i]);
+                if (EXACT || k < ncur) madd_lazy(acc[k], wgt, rowp[(size_t)k * SV + i]);
             }
           }
         }
       }
+      // (float-float: the per-lane sums of at most width x width terms close here)
+#pragma unroll
+      for (int k = 0; k < CMAX; ++k) acc[k] = renorm_val(acc[k]);
       // reduce within the point's lane group
       if constexpr (use_transpose<T, D, CMAX>()) {
         constexpr int RP = CMAX | 1;   // odd pitch: the 32 lanes write to 32 banks

@@ -116,6 +116,25 @@ __device__ __forceinline__ dd ldg_val<dd>(const dd* p) {
   return {u.x, u.y};
 }
 
+// acc += a b without renormalising float-float sums; renorm_val() closes them (identity for
+// float and double)
+template <typename T>
+__device__ __forceinline__ void madd_lazy(T& acc, T a, T b) {
+  acc += a * b;
+}
+template <>
+__device__ __forceinline__ void madd_lazy<dd>(dd& acc, dd a, dd b) {
+  acc = fma_dd_lazy(a, b, acc);
+}
+template <typename T>
+__device__ __forceinline__ T renorm_val(T v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ dd renorm_val<dd>(dd v) {
+  return renorm(v);
+}
+
 // A plan value to float64
 template <typename T>
 __device__ __forceinline__ double to_f64(T v) {

@@ -245,8 +245,24 @@ __global__ void __launch_bounds__(256) k_spread2d(Spread2Args<T> a) {
       for (int rr = 0; rr < RPW; ++rr) {
         const T v = px * pyr[rr];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) madd(acc[rr][k], v, wk[k]);
+        for (int k = 0; k < NC; ++k) madd_lazy(acc[rr][k], v, wk[k]);
       }
+      if constexpr (is_dd<T>::value) {
+        // float-float sums: renormalise every eight points (the low word then stays within a
+        // few ulps of the high one)
+        if ((j & 7) == 7) {
+#pragma unroll
+          for (int rr = 0; rr < RPW; ++rr)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) acc[rr][k] = renorm_val(acc[rr][k]);
+        }
+      }
+    }
+    if constexpr (is_dd<T>::value) {
+#pragma unroll
+      for (int rr = 0; rr < RPW; ++rr)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[rr][k] = renorm_val(acc[rr][k]);
     }
     __syncthreads();  // slots, lists and counters are refilled by the next round
   }
