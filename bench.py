@@ -781,6 +781,8 @@ def run_solve_compare(args):
     import torch
     import paper_2407_03608_gb300 as gpn
     from paper_2407_03608_gb300 import abi
+    if args.d == 3:
+        return run_solve_3d(args)
     dev = torch.device("cuda", 0)
     w = workload(args)
     pts, s_, l_, y = (torch.from_numpy(v).to(dev) for v in (w.points, w.s, w.l, w.y))
@@ -817,6 +819,33 @@ def run_solve_compare(args):
     p64.close()
     hi.close()
     print(json.dumps(out), flush=True)
+
+
+def run_solve_3d(args, maxit=3000, outer_max=6):
+    """The 3-D workload (N = 2e6 uniform, Matern 5/2, eps = 1e-6): the refined solve (FP32
+    inner CG, residuals on the float64 plan) to relative residual --rtol, timed.  Both plans
+    use the memory-lean step 3, so that they fit one GB300 together (78 + 155 GB); the inner
+    iterations of each refinement step are capped at `maxit`, and the steps at `outer_max`,
+    to bound the run (status GP_ENOTCONV then, with the float64 residual reached)."""
+    import torch
+    import gpinputs
+    import paper_2407_03608_gb300 as gpn
+    dev = torch.device("cuda", 0)
+    w = gpinputs.config_3d()
+    pts, s_, l_, y = (torch.from_numpy(v).to(dev) for v in (w.points, w.s, w.l, w.y))
+    lo = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, step3=2)
+    hi = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP64, step3=2, **lo.matched_opts())
+    out = {"workload": w.name, "rtol": args.rtol, "nf": lo.info["nf"], "M": lo.info["M"],
+           "bytes_resident": int(lo.info["bytes_resident"] + hi.info["bytes_resident"])}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, info = hi.solve_refined(lo, y, w.eta ** 2, rtol=args.rtol, maxit=maxit, outer_max=outer_max)
+    torch.cuda.synchronize()
+    out["refined_fp32_inner"] = {"seconds": round(time.perf_counter() - t0, 3), "inner_iters": int(info["iters"][0]),
+                                 "relres_fp64": float(info["relres"][0]), "status": int(info["status"])}
+    print(json.dumps(out), flush=True)
+    lo.close()
+    hi.close()
 
 
 def main():
