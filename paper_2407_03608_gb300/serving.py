@@ -31,6 +31,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import sys
 import threading
 import time
 from collections import OrderedDict
@@ -241,6 +242,7 @@ class Server:
         self.cache = PlanCache(self.budget) if cache_plans else None
         self.max_rhs = max_rhs
         self.rhs_block = rhs_block
+        self.progress = False          # serve(): one JSON line per served request on stderr
 
     def _build_pair(self, req, stream_handle=None):
         """The FP64 (residual) and FP32 (inner CG) plans of a request at the finest eps that
@@ -433,6 +435,9 @@ class Server:
             done.append(rec)
             if check_every and i % check_every == 0 and not rec.rejected:
                 errs.append(self.check_vs_fp64(r, alpha))
+            if self.progress:
+                print(json.dumps(dict(rec.__dict__, err_vs_fp64=errs[-1] if check_every and i % check_every == 0
+                                      and not rec.rejected else None)), file=sys.stderr, flush=True)
         rejected = [s for s in done if s.rejected]
         done = [s for s in done if not s.rejected]
         requests = [r for r in requests if r.rid not in {s.rid for s in rejected}]
@@ -558,6 +563,7 @@ def main():
     ap.add_argument("--cache", action="store_true", help="keep each model's plans resident (PlanCache)")
     ap.add_argument("--check-every", type=int, default=0,
                     help="compare every k-th served solution with the plain float64 GPU solve")
+    ap.add_argument("--progress", action="store_true", help="one JSON line per served request on stderr")
     args = ap.parse_args()
     import gpinputs
     reqs = gpinputs.serving_stream(args.requests, n_min=int(args.n_min), n_max=int(args.n_max), seed=args.seed,
@@ -565,6 +571,7 @@ def main():
                                    nus=tuple(float(v) for v in args.nus.split(",")), n_models=args.models)
     srv = Server(hbm_budget=args.budget_gb * 1e9, eps_target=args.eps, cache_plans=args.cache,
                  max_rhs=args.max_rhs)
+    srv.progress = args.progress
     if args.slots > 0:
         out = srv.serve_batched(reqs, load=args.load, slots=args.slots)
     else:
