@@ -31,6 +31,7 @@ Modules:
   rows        exact sampled rows of K alpha (C, OpenMP) for large N
   bounds      the error quantities of Sec. 5 (Definition eptrap; Lemma interp)
   diagcorr    the exact diagonal K~_ii and the diagonal-corrected matvec (an extension)
+  nearfield   K~ for single pairs (separable form) and the near-field-corrected matvec (an extension)
   variance    posterior variance at the training points and its probe estimator (an extension)
 """
 from . import matern, kernel, quadrature, chebyshev, nudft, ktilde, bounds, rows  # noqa: F401
