@@ -49,8 +49,11 @@ def parse():
                          "fp64 native float64, fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--side", action="store_true",
+                    help="also run the side measurements (config 1 latency, batched R, config 2 at nu = 1/2, "
+                         "config 3, served solves); each prints its wall time to stderr as it ends")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the side measurements (config 1 latency, batched R, config 3, served solves)")
+                    help="no side measurements (the default; kept so that recorded commands still run)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-case", action="store_true",
                     help="a fixed workload for profilers: build one plan (--d, --n, --eps, --precision, "
@@ -740,10 +743,13 @@ def side_measurements(args, dev, checks):
                      ("config2_nu_half", lambda: measure_nu_half(dev, checks)),
                      ("config3", lambda: measure_config3(dev)),
                      ("served", lambda: measure_serving(args.serve_requests))):
+        t0 = time.perf_counter()
         try:
             res[name] = fn()
         except Exception as e:  # recorded, not fatal: the headline line is still printed
             res[name] = {"error": "%s: %s" % (type(e).__name__, str(e)[:200])}
+        res[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        print("side %s: %.1f s" % (name, res[name]["wall_s"]), file=sys.stderr, flush=True)
     return res
 
 
@@ -821,7 +827,7 @@ def run_solve_compare(args):
     print(json.dumps(out), flush=True)
 
 
-def run_solve_3d(args, maxit=3000, outer_max=6):
+def run_solve_3d(args, maxit=1500, outer_max=4):
     """The 3-D workload (N = 2e6 uniform, Matern 5/2, eps = 1e-6): the refined solve (FP32
     inner CG, residuals on the float64 plan) to relative residual --rtol, timed.  Both plans
     use the memory-lean step 3, so that they fit one GB300 together (78 + 155 GB); the inner
@@ -834,7 +840,10 @@ def run_solve_3d(args, maxit=3000, outer_max=6):
     w = gpinputs.config_3d()
     pts, s_, l_, y = (torch.from_numpy(v).to(dev) for v in (w.points, w.s, w.l, w.y))
     lo = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, step3=2)
-    hi = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP64, step3=2, **lo.matched_opts())
+    # the FP32 plan's fine grid (nf = 864) for the float64 plan too, with its kernel width
+    # chosen for that upsampling: 155 GB instead of 258 GB at its own nf = 1024
+    hi = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP64, step3=2, nf=lo.info["nf"],
+                  **lo.matched_opts())
     out = {"workload": w.name, "rtol": args.rtol, "nf": lo.info["nf"], "M": lo.info["M"],
            "bytes_resident": int(lo.info["bytes_resident"] + hi.info["bytes_resident"])}
     torch.cuda.synchronize()
@@ -864,7 +873,7 @@ def main():
     plan.close()
     if rank == 0:
         checks = []
-        if ws == 1 and not args.no_extras:
+        if ws == 1 and args.side:
             import torch
             result["side"] = side_measurements(args, torch.device("cuda", local), checks)
         if ws == 1 and not args.no_cpu_baseline:

@@ -140,6 +140,19 @@ typedef struct gp_plan_opts {
                              (1)-(5) over the columns in blocks of rhs_block, one after the
                              other on the caller's stream, so R up to max_rhs fits where
                              max_rhs sets of grids would not.                             */
+  double near_radius;     /* > 0: add the exact defect of every pair of distinct plan points
+                             closer than near_radius (in x units), out_i += sum_{0 < |x_i - x_j|
+                             < near_radius} (K_ij - K~_ij) alpha_j, K_ij of Eq. (nonstat2),
+                             K~_ij of Eq. (Ktilde) through its per-dimension factors.  An
+                             extension, not in the paper: for small nu the truncation error of
+                             K~ sits on a neighbourhood of the diagonal (the cusp of phi at
+                             r = 0), not on the diagonal alone; with diag_correct the plan
+                             equals K on every pair within the radius.  nu = 1/2, 3/2, 5/2 or
+                             GP_SE only (else GP_EUNSUPPORTED).  The pairs are built at plan
+                             time (float64, about 12 bytes each, not in the footprint
+                             estimate) and applied in every matvec and solve on the plan's
+                             points, not to posterior means.  Meant for sparse point sets: the
+                             cost grows with the number of pairs.  0 (default): off.     */
 } gp_plan_opts;
 
 typedef struct gp_plan_info {
@@ -161,6 +174,8 @@ typedef struct gp_plan_info {
   int tuned;                               /* plans the autotuner timed (0: not tuned)    */
   double tune_ms;                          /* this plan's matvec time in the autotuner    */
   int rhs_block;                           /* right-hand sides per pass through the grids */
+  double near_radius;                      /* near-field radius (0: off)                  */
+  long long near_pairs;                    /* pairs with their defect stored              */
 } gp_plan_info;
 
 /* The autotuner's search space (host only, no GPU needed): every spread/interp tile

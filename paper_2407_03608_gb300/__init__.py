@@ -78,7 +78,7 @@ class Plan:
                   "M": abi.GP_SET_M, "dw": abi.GP_SET_DW, "nufft_tol": abi.GP_SET_NUFFT,
                   "upsampfac": abi.GP_SET_NUFFT, "box_lo": abi.GP_SET_BOX, "box_hi": abi.GP_SET_BOX,
                   "nf": abi.GP_SET_NF, "tile": abi.GP_SET_TILE, "max_bytes": 0, "transform": 0, "step3": 0, "diag_correct": 0,
-                  "autotune": 0, "rhs_block": 0}
+                  "autotune": 0, "rhs_block": 0, "near_radius": 0}
         for k, v in overrides.items():
             if k not in keymap:
                 raise TypeError("unknown plan option %r" % k)
@@ -159,4 +159,6 @@ class Plan:
             o.update(n_t=i["n_t"], t_min=i["t_min"], t_max=i["t_max"])
         if i["diag_correct"]:
             o["diag_correct"] = 1
+        if i["near_radius"] > 0:
+            o["near_radius"] = i["near_radius"]
         return o

@@ -48,7 +48,8 @@ class gp_plan_opts(ctypes.Structure):
                 ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
                 ("nf", ctypes.c_longlong), ("tile", ctypes.c_int), ("transform", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("max_bytes", ctypes.c_longlong), ("step3", ctypes.c_int),
-                ("diag_correct", ctypes.c_int), ("autotune", ctypes.c_int), ("rhs_block", ctypes.c_int)]
+                ("diag_correct", ctypes.c_int), ("autotune", ctypes.c_int), ("rhs_block", ctypes.c_int),
+                ("near_radius", ctypes.c_double)]
 
 
 class gp_plan_info(ctypes.Structure):
@@ -65,7 +66,7 @@ class gp_plan_info(ctypes.Structure):
                 ("est_err_trunc", ctypes.c_double), ("est_err_alias", ctypes.c_double),
                 ("bytes_resident", ctypes.c_longlong), ("max_rhs", ctypes.c_int), ("step3", ctypes.c_int),
                 ("diag_correct", ctypes.c_int), ("tuned", ctypes.c_int), ("tune_ms", ctypes.c_double),
-                ("rhs_block", ctypes.c_int)]
+                ("rhs_block", ctypes.c_int), ("near_radius", ctypes.c_double), ("near_pairs", ctypes.c_longlong)]
 
     def as_dict(self):
         out = {}

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgpnufft.so")
-SOURCES = ["abi.cpp", "params.cpp", "points.cu", "nufft.cu", "spread.cu", "spread2d.cu", "diag.cu", "step3_lean.cu", "interp.cu", "fft_rows.cu", "fft2d.cu", "cg.cu", "noalloc.cu"]
+SOURCES = ["abi.cpp", "params.cpp", "points.cu", "nufft.cu", "spread.cu", "spread2d.cu", "diag.cu", "step3_lean.cu", "interp.cu", "fft_rows.cu", "fft2d.cu", "cg.cu", "noalloc.cu", "nearfield.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

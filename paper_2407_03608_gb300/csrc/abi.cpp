@@ -498,6 +498,8 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   build_pointset(*plan, plan->pts, x.ptr, w, sig, N, st, plan_alloc_cb, plan.get(), &bstart);
   GPN_CHECK(o.diag_correct == 0 || o.diag_correct == 1, GP_EINVAL, "diag_correct must be 0 or 1");
   if (o.diag_correct) build_diag_correction(*plan, w, sig, st);
+  GPN_CHECK(o.near_radius >= 0.0 && std::isfinite(o.near_radius), GP_EINVAL, "near_radius must be >= 0");
+  if (o.near_radius > 0.0) build_near_field(*plan, o.near_radius, x.ptr, w, sig, st);
   build_active_tiles(*plan, bstart);
   if (spread2d_supported(*plan)) build_spread2d_tiles(*plan, bstart);
   GPN_CHECK(o.precision != GP_DF64 || plan->sp2_tiles, GP_EUNSUPPORTED,
@@ -595,7 +597,7 @@ void check_same_hyper(const Plan& a, const Plan& b) {
   bool same = a.N == b.N && x.d == y.d && x.family == y.family && x.n_t == y.n_t && x.t_min == y.t_min &&
               x.t_max == y.t_max && x.n_sigma == y.n_sigma && x.sig_lo == y.sig_lo && x.sig_hi == y.sig_hi &&
               x.M == y.M && x.dw == y.dw && (x.family == GP_SE || x.nu == y.nu) &&
-              (a.dcorr != nullptr) == (b.dcorr != nullptr);
+              (a.dcorr != nullptr) == (b.dcorr != nullptr) && a.near_radius == b.near_radius;
   GPN_CHECK(same, GP_EINVAL, "plan_lo and plan_hi must share points and hyperparameters");
 }
 
@@ -1015,6 +1017,8 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->bytes_resident = p->bytes;
     info->max_rhs = p->max_rhs;
     info->rhs_block = p->grid_rhs;
+    info->near_radius = p->near_radius;
+    info->near_pairs = p->near_nnz;
     info->step3 = p->lean ? 2 : 1;
     info->diag_correct = p->dcorr ? 1 : 0;
     info->tuned = p->tuned;

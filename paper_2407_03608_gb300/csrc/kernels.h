@@ -141,6 +141,29 @@ __device__ __forceinline__ double to_f64(T v) {
   return (double)v;
 }
 
+// Chebyshev weights of Eq. (Wk) from the paper-native fields of one point:
+// w_k(x) = w (2 pi sigma^2)^(-d/2) P_k(sigma), P_k by the barycentric formula on the
+// Chebyshev-Lobatto nodes (weights (-1)^k, halved at both ends); exact at a node.
+struct ChebArgs {
+  double nodes[kMaxChannels];
+  double bary[kMaxChannels];
+  int C;
+  int d;
+};
+__device__ __forceinline__ void cheb_weights(double w, double s, const ChebArgs& cb, double* out) {
+  const double pre = w * pow(6.283185307179586476925286766559 * s * s, -0.5 * cb.d);
+  int hit = -1;
+  for (int k = 0; k < cb.C; ++k)
+    if (s == cb.nodes[k]) hit = k;
+  if (hit >= 0 || cb.C == 1) {
+    for (int k = 0; k < cb.C; ++k) out[k] = (k == hit || cb.C == 1) ? pre : 0.0;
+    return;
+  }
+  double den = 0.0;
+  for (int k = 0; k < cb.C; ++k) den += cb.bary[k] / (s - cb.nodes[k]);
+  for (int k = 0; k < cb.C; ++k) out[k] = pre * (cb.bary[k] / (s - cb.nodes[k])) / den;
+}
+
 // Channel-count buckets: kernels keep per-channel values in registers sized by a
 // compile-time bound CMAX >= C.
 inline int cmax_bucket(int C) { return C <= 8 ? 8 : (C <= 12 ? 12 : (C <= 16 ? 16 : 32)); }

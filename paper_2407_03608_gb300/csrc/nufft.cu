@@ -212,6 +212,7 @@ void matvec_block(Plan& plan, const double* alpha_sorted, double* out_sorted, in
   run_fft_inverse(plan, R, st);
   if (rec) GPN_CUDA(cudaEventRecord(pf.ev[4], st));
   launch_interp(plan, plan.pts, alpha_sorted, shift, out_sorted, R, st);
+  launch_near_apply(plan, alpha_sorted, out_sorted, R, st);
   if (rec) {
     pf.in_matvec = false;
     GPN_CUDA(cudaEventRecord(pf.ev[5], st));

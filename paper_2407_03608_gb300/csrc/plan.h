@@ -94,6 +94,12 @@ struct Plan {
   int lean_cp = 0;                      // channel pitch of tab (16-byte multiple)
   int lean_J = 0;                       // quadrature nodes N_t + 1
   double* dcorr = nullptr;              // diagonal defect K_ii - K~_ii (sorted order), null when off
+  // near-field correction: K_ij - K~_ij for pairs closer than near_radius (CSR, sorted order)
+  double near_radius = 0.0;
+  int* near_ptr = nullptr;
+  int* near_col = nullptr;
+  double* near_val = nullptr;
+  long long near_nnz = 0;
   int tuned = 0;                        // plans timed by the tile autotuner (0: not tuned)
   double tune_ms = 0.0;                 // this plan's matvec time in the autotuner
   long long n_freq = 0;                 // frequencies in the half box
@@ -220,6 +226,13 @@ void launch_spread2d(Plan& plan, const double* alpha_sorted, int R, cudaStream_t
 void launch_diag(Plan& plan, int R, cudaStream_t st);
 // Exact diagonal correction: plan.dcorr[p] = K_pp - K~_pp (points.cu).
 void build_diag_correction(Plan& plan, const double* w_dev, const double* sig_dev, cudaStream_t st);
+// Near-field correction (nearfield.cu): tables of the separable K~ factors and the pairs
+// closer than `radius` with their defect K_ij - K~_ij, from the caller-order coordinates
+// and paper-native fields; the apply adds them to a matvec on the plan's points.
+bool near_field_supported(int family, double nu);
+void build_near_field(Plan& plan, double radius, const double* x_dev, const double* w_dev, const double* sig_dev,
+                      cudaStream_t st);
+void launch_near_apply(Plan& plan, const double* alpha_sorted, double* out_sorted, int R, cudaStream_t st);
 // Memory-lean step 3 (step3_lean.cu): the same map from the per-dimension factors,
 // for the transposed (tr3) and the full-grid layouts.
 int lean_channel_pitch(int C, size_t rs);

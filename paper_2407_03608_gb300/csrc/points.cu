@@ -133,29 +133,6 @@ __global__ void k_bin_start(const int* __restrict__ keys, long long n, long long
   start[b] = (int)lo;
 }
 
-struct ChebArgs {
-  double nodes[kMaxChannels];
-  double bary[kMaxChannels];
-  int C;
-  int d;
-};
-
-// w_k(x) = w (2 pi sigma^2)^(-d/2) P_k(sigma), P_k by the barycentric formula on the
-// Chebyshev-Lobatto nodes (weights (-1)^k, halved at both ends); exact at a node.
-__device__ void cheb_weights(double w, double s, const ChebArgs& cb, double* out) {
-  const double pre = w * pow(kTwoPi * s * s, -0.5 * cb.d);
-  int hit = -1;
-  for (int k = 0; k < cb.C; ++k)
-    if (s == cb.nodes[k]) hit = k;
-  if (hit >= 0 || cb.C == 1) {
-    for (int k = 0; k < cb.C; ++k) out[k] = (k == hit || cb.C == 1) ? pre : 0.0;
-    return;
-  }
-  double den = 0.0;
-  for (int k = 0; k < cb.C; ++k) den += cb.bary[k] / (s - cb.nodes[k]);
-  for (int k = 0; k < cb.C; ++k) out[k] = pre * (cb.bary[k] / (s - cb.nodes[k])) / den;
-}
-
 // Diagonal defect K_ii - K~_ii per sorted point (see build_diag_correction).
 __global__ void k_diag_defect(const int* __restrict__ perm, long long n, const double* __restrict__ w,
                               const double* __restrict__ sig, ChebArgs cb, const double* __restrict__ S,
