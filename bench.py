@@ -641,37 +641,44 @@ def measure_batched(dev, n, block=8, steps=2):
 
 
 def measure_config3(dev, steps=3):
-    """d=3, N=2e6 uniform, Matern 5/2, eps=1e-6, FP32: one CG iteration."""
+    """d=3, N=2e6 uniform, Matern 5/2, eps=1e-6, FP32: one CG iteration, with the 3-D cuFFT
+    transforms and with the split ones (last axis 1-D, then a strided 2-D transform over the
+    half-spectrum columns 0..M only), each with the stored A' tensor and with the memory-lean
+    step 3, and the per-phase milliseconds of each (the library's own events)."""
     import torch
     import gpinputs
     import paper_2407_03608_gb300 as gpn
     from paper_2407_03608_gb300 import abi
     w = gpinputs.config_3d()
-    t0 = time.perf_counter()
-    plan = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
-                    torch.from_numpy(w.l).to(dev), nu=w.nu, eps=w.eps, precision=gpn.GP_FP32)
-    torch.cuda.synchronize()
-    plan_s = time.perf_counter() - t0
+    pts, s_, l_ = (torch.from_numpy(v).to(dev) for v in (w.points, w.s, w.l))
     y = torch.from_numpy(w.y).to(dev)
     x = torch.empty_like(y)
-    abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, 1)
-    ms = _events_ms(lambda: abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, steps), 1) / steps
-    i = plan.info
-    opts = plan.matched_opts()
-    plan.close()
-    # the same plan with the memory-lean step 3 (no A' tensor)
-    lean = gpn.Plan(torch.from_numpy(w.points).to(dev), torch.from_numpy(w.s).to(dev),
-                    torch.from_numpy(w.l).to(dev), nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, step3=2, **opts)
-    abi.gp_cg_solve(lean.handle, y, x, 1, w.eta ** 2, 1e-30, 1)
-    ms_lean = _events_ms(lambda: abi.gp_cg_solve(lean.handle, y, x, 1, w.eta ** 2, 1e-30, steps), 1) / steps
-    lean_bytes = int(lean.info["bytes_resident"])
-    lean.close()
-    return {"workload": w.name, "precision": "fp32 (f64 CG)", "ms_per_step": round(ms, 3),
-            "value": round(w.N / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "plan_seconds": round(plan_s, 3),
-            "nf": i["nf"], "M": i["M"], "n_sigma": i["n_sigma"], "kernel_width": i["kernel_width"],
-            "bytes_resident": int(i["bytes_resident"]),
-            "memory_lean_step3": {"ms_per_step": round(ms_lean, 3), "value": round(w.N / (ms_lean * 1e-3) / 1e6, 3),
-                                  "bytes_resident": lean_bytes}}
+    out = {"workload": w.name, "precision": "fp32 (f64 CG)", "unit": UNIT}
+    opts = None
+    for name, tr, s3 in (("cufft3d", 1, 1), ("split", 4, 1), ("cufft3d_memory_lean_step3", 1, 2),
+                         ("split_memory_lean_step3", 4, 2)):
+        t0 = time.perf_counter()
+        plan = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, transform=tr, step3=s3,
+                        **(opts or {}))
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        if opts is None:
+            i = plan.info
+            opts = dict(plan.matched_opts(), nf=i["nf"])
+            out.update(nf=i["nf"], M=i["M"], n_sigma=i["n_sigma"], kernel_width=i["kernel_width"])
+        abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, 1)
+        ms = _events_ms(lambda: abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, steps), 1) / steps
+        phase_ms, _, n_rec = _phases(abi, plan, y, x, w.eta ** 2, 2)
+        out[name] = {"transform": tr, "step3": s3, "ms_per_step": round(ms, 3),
+                     "value": round(w.N / (ms * 1e-3) / 1e6, 3), "plan_seconds": round(plan_s, 3),
+                     "bytes_resident": int(plan.info["bytes_resident"]),
+                     "phase_ms": dict(zip(("spread", "fft_fwd", "step3", "fft_inv", "interp"),
+                                          (round(v, 3) for v in phase_ms)))}
+        plan.close()
+        torch.cuda.empty_cache()
+    best = min((v for v in out.values() if isinstance(v, dict)), key=lambda v: v["ms_per_step"])
+    out["ms_per_step"], out["value"] = best["ms_per_step"], best["value"]
+    return out
 
 
 def measure_serving(n_requests, n_models=8):
@@ -701,11 +708,13 @@ def measure_serving(n_requests, n_models=8):
     return out
 
 
-def measure_nu_half(dev, checks, eps=5e-3):
+def measure_nu_half(dev, checks, eps=5e-3, near_radius=2e-3):
     """The 2-D clustered workload at nu = 1/2 on the largest grid that fits one GB300 (eps =
     5e-3: nf = 32768, M = 6944; eps = 2.5e-3 would need nf = 65536, 560 GB in FP64): one
-    matvec of each of FP64, FP32, and both with the exact diagonal correction, timed, and
-    their outputs kept for the CPU-baseline leg to compare with exact rows of K alpha.
+    matvec of each of FP64, FP32, both with the exact diagonal correction, and FP64 with the
+    diagonal and the near-field correction (pairs closer than near_radius, about ten grid
+    wavelengths 1/(M dw)), timed, and their outputs kept for the CPU-baseline leg to compare
+    with exact rows of K alpha.
     For nu = 1/2 the mode count grows like eps^-1 (Sec. 5.4), so 1e-6 is out of reach."""
     import torch
     import gpinputs
@@ -715,12 +724,17 @@ def measure_nu_half(dev, checks, eps=5e-3):
     a = torch.from_numpy(w.alpha).to(dev)
     out = {"workload": w.name, "eps": eps}
     opts = None
-    for name, prec, dc in (("fp64", gpn.GP_FP64, 0), ("fp64_diag_correct", gpn.GP_FP64, 1),
-                           ("fp32", gpn.GP_FP32, 0), ("fp32_diag_correct", gpn.GP_FP32, 1)):
+    for name, prec, dc, r_c in (("fp64", gpn.GP_FP64, 0, 0.0), ("fp64_diag_correct", gpn.GP_FP64, 1, 0.0),
+                                ("fp64_diag_near_2e-3", gpn.GP_FP64, 1, near_radius),
+                                ("fp32", gpn.GP_FP32, 0, 0.0), ("fp32_diag_correct", gpn.GP_FP32, 1, 0.0)):
         kw = dict(opts or {})
         if dc:
             kw["diag_correct"] = 1
+        if r_c > 0:
+            kw["near_radius"] = r_c
+        t0 = time.perf_counter()
         pl = gpn.Plan(pts, s_, l_, nu=0.5, eps=eps, precision=prec, **kw)
+        plan_s = time.perf_counter() - t0
         if opts is None:
             opts = {k: v for k, v in pl.matched_opts().items() if k != "diag_correct"}
             i = pl.info
@@ -729,7 +743,10 @@ def measure_nu_half(dev, checks, eps=5e-3):
         pl.matvec(a)
         ms = _events_ms(lambda: pl.matvec(a), 2)
         res = pl.matvec(a).cpu().numpy()
-        out[name] = {"ms_per_matvec": round(ms, 3), "bytes_resident": int(pl.info["bytes_resident"])}
+        out[name] = {"ms_per_matvec": round(ms, 3), "bytes_resident": int(pl.info["bytes_resident"]),
+                     "plan_seconds": round(plan_s, 2)}
+        if r_c > 0:
+            out[name]["near_pairs"] = int(pl.info["near_pairs"])
         checks.append(("config2_nu_half." + name, w, res))
         pl.close()
         torch.cuda.empty_cache()
@@ -827,7 +844,7 @@ def run_solve_compare(args):
     print(json.dumps(out), flush=True)
 
 
-def run_solve_3d(args, maxit=1500, outer_max=4):
+def run_solve_3d(args, maxit=400, outer_max=4):
     """The 3-D workload (N = 2e6 uniform, Matern 5/2, eps = 1e-6): the refined solve (FP32
     inner CG, residuals on the float64 plan) to relative residual --rtol, timed.  Both plans
     use the memory-lean step 3, so that they fit one GB300 together (78 + 155 GB); the inner
