@@ -54,7 +54,7 @@ def parse():
                          "config 3, served solves); each prints its wall time to stderr as it ends")
     ap.add_argument("--no-extras", action="store_true",
                     help="no side measurements (the default; kept so that recorded commands still run)")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=12)
     ap.add_argument("--profile-case", action="store_true",
                     help="a fixed workload for profilers: build one plan (--d, --n, --eps, --precision, "
                          "--transform) and run --matvecs matvecs, nothing else")
@@ -641,10 +641,9 @@ def measure_batched(dev, n, block=8, steps=2):
 
 
 def measure_config3(dev, steps=3):
-    """d=3, N=2e6 uniform, Matern 5/2, eps=1e-6, FP32: one CG iteration, with the 3-D cuFFT
-    transforms and with the split ones (last axis 1-D, then a strided 2-D transform over the
-    half-spectrum columns 0..M only), each with the stored A' tensor and with the memory-lean
-    step 3, and the per-phase milliseconds of each (the library's own events)."""
+    """d=3, N=2e6 uniform, Matern 5/2, eps=1e-6, FP32: one CG iteration with the stored A'
+    tensor and with the memory-lean step 3, and the per-phase milliseconds of each (the
+    library's own events)."""
     import torch
     import gpinputs
     import paper_2407_03608_gb300 as gpn
@@ -655,11 +654,9 @@ def measure_config3(dev, steps=3):
     x = torch.empty_like(y)
     out = {"workload": w.name, "precision": "fp32 (f64 CG)", "unit": UNIT}
     opts = None
-    for name, tr, s3 in (("cufft3d", 1, 1), ("split", 4, 1), ("cufft3d_memory_lean_step3", 1, 2),
-                         ("split_memory_lean_step3", 4, 2)):
+    for name, s3 in (("stored_a", 1), ("memory_lean_step3", 2)):
         t0 = time.perf_counter()
-        plan = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, transform=tr, step3=s3,
-                        **(opts or {}))
+        plan = gpn.Plan(pts, s_, l_, nu=w.nu, eps=w.eps, precision=gpn.GP_FP32, step3=s3, **(opts or {}))
         torch.cuda.synchronize()
         plan_s = time.perf_counter() - t0
         if opts is None:
@@ -669,7 +666,7 @@ def measure_config3(dev, steps=3):
         abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, 1)
         ms = _events_ms(lambda: abi.gp_cg_solve(plan.handle, y, x, 1, w.eta ** 2, 1e-30, steps), 1) / steps
         phase_ms, _, n_rec = _phases(abi, plan, y, x, w.eta ** 2, 2)
-        out[name] = {"transform": tr, "step3": s3, "ms_per_step": round(ms, 3),
+        out[name] = {"step3": s3, "ms_per_step": round(ms, 3),
                      "value": round(w.N / (ms * 1e-3) / 1e6, 3), "plan_seconds": round(plan_s, 3),
                      "bytes_resident": int(plan.info["bytes_resident"]),
                      "phase_ms": dict(zip(("spread", "fft_fwd", "step3", "fft_inv", "interp"),
@@ -681,7 +678,7 @@ def measure_config3(dev, steps=3):
     return out
 
 
-def measure_serving(n_requests, n_models=8):
+def measure_serving(n_requests, n_models=6, max_rhs=4):
     """A bounded sample of the serving stream: requests on `n_models` models (points, fields,
     nu; popularity 1/k), solved to rtol 1e-8 (FP32 CG inside float64 refinement) with each
     model's plans kept resident (PlanCache, 120 GB budget); p50/p99 latency at 80% of the
@@ -690,7 +687,7 @@ def measure_serving(n_requests, n_models=8):
     import gpinputs
     from paper_2407_03608_gb300.serving import Server
     reqs = gpinputs.serving_stream(n_requests, n_min=1000, n_max=20_000, dims=(1, 2), nus=(0.5, 1.5, 2.5),
-                                   max_rhs=16, n_models=n_models)
+                                   max_rhs=max_rhs, n_models=n_models)
     srv = Server(hbm_budget=120e9, eps_target=1e-6, cache_plans=True)
     out = srv.serve(reqs, load=0.8, check_every=10)
     out.pop("records")
@@ -703,8 +700,9 @@ def measure_serving(n_requests, n_models=8):
     out["continuous_batching"] = srv.serve_batched(reqs, load=0.8, slots=3)
     srv.cache.clear()
     out["sample"] = ("%d requests of the serving stream (seed 100) on %d models: N log-uniform in [1e3, 2e4], "
-                     "d in {1, 2}, nu in {1/2, 3/2, 5/2}, R in 1..16 (3-D models: a separate run, their grids "
-                     "cost seconds an iteration)" % (n_requests, n_models))
+                     "d in {1, 2}, nu in {1/2, 3/2, 5/2}, R in 1..%d (a 2-D model's grid is as large as the "
+                     "N = 1e6 workload's, so a request costs seconds per right-hand side; 3-D models cost "
+                     "minutes)" % (n_requests, n_models, max_rhs))
     return out
 
 
@@ -766,7 +764,7 @@ def side_measurements(args, dev, checks):
         except Exception as e:  # recorded, not fatal: the headline line is still printed
             res[name] = {"error": "%s: %s" % (type(e).__name__, str(e)[:200])}
         res[name]["wall_s"] = round(time.perf_counter() - t0, 1)
-        print("side %s: %.1f s" % (name, res[name]["wall_s"]), file=sys.stderr, flush=True)
+        print("side %s: %.1f s %s" % (name, res[name]["wall_s"], json.dumps(res[name])), file=sys.stderr, flush=True)
     return res
 
 

@@ -103,11 +103,7 @@ typedef struct gp_plan_opts {
                                cuFFT along the first axis (d <= 2, nf = 2^a);
                              3 pruned, transposed (d = 2, nf = 2^a): custom row FFTs
                                write columns of modes 0..M, cuFFT transforms each
-                               contiguous column, step 3 on the mode box only;
-                             4 split full grid (d = 3): cuFFT 1-D R2C/C2R along the
-                               last axis over every row, then a strided 2-D C2C over
-                               the first two axes of the half-spectrum columns 0..M
-                               only (the others are zeroed by step 3)             */
+                               contiguous column, step 3 on the mode box only    */
   int max_rhs;            /* largest R the plan will be called with (default 1)         */
   long long max_bytes;    /* refuse plans whose resident device bytes exceed this (0 = no limit) */
   int step3;              /* step (3) of Sec. 4.2:
@@ -168,7 +164,7 @@ typedef struct gp_plan_info {
   int kernel_width; double kernel_beta;    /* exponential-of-semicircle spreading kernel  */
   double upsampfac; double nufft_tol;
   int tile;                                /* spread/interp tile edge (cells)             */
-  int transform;                           /* transform mode in use (1, 2, 3 or 4)        */
+  int transform;                           /* transform mode in use (1, 2 or 3)           */
   double box_lo[3], box_hi[3];             /* region points and queries must lie in       */
   double est_err_t, est_err_sigma, est_err_trunc, est_err_alias; /* stage estimates, relative entrywise */
   long long bytes_resident;                /* device bytes the plan holds                 */

@@ -174,7 +174,6 @@ Plan::~Plan() {
   for (auto& kv : fft_inv) cufftDestroy(kv.second);
   for (auto& kv : fft_col) cufftDestroy(kv.second);
   for (auto& kv : fft_t3) cufftDestroy(kv.second);
-  if (fft_yz_made) cufftDestroy(fft_yz);
   if (cg_graph.exec) cudaGraphExecDestroy(cg_graph.exec);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   for (void* p : owned) cudaFree(p);
@@ -380,8 +379,7 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   long long nfreq = 1;
   for (int q = 0; q < d - 1; ++q) nfreq *= (2 * h.M + 1);
   nfreq *= (h.M + 1);
-  GPN_CHECK(o.transform >= 0 && o.transform <= 4, GP_EINVAL, "transform must be 0, 1, 2, 3 or 4");
-  GPN_CHECK(o.transform != 4 || d == 3, GP_EUNSUPPORTED, "split full-grid transforms (transform 4) need d = 3");
+  GPN_CHECK(o.transform >= 0 && o.transform <= 3, GP_EINVAL, "transform must be 0, 1, 2 or 3");
   const bool ddp = o.precision == GP_DF64;
   const bool row_ok = !ddp && rowfft_supported(d, h.nf, rs);
   const bool t3_ok = tr3_supported(d, h.nf, o.precision);
@@ -393,7 +391,6 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   // d = 1 in FP64 (FP64 FFT arithmetic is ALU-bound on GB300); else full-grid cuFFT
   ps.tr3 = o.transform == 3 || (o.transform == 0 && t3_ok);
   ps.rowfft = o.transform == 2 || (o.transform == 0 && !ps.tr3 && row_ok && o.precision == GP_FP64);
-  ps.split3 = o.transform == 4;
   if (ps.tr3) nfreq = (h.M + 1) * (h.M + 1);
   ps.G = G;
   ps.S = S;
@@ -416,7 +413,7 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   // device memory
   GPN_CHECK(o.step3 >= 0 && o.step3 <= 2, GP_EINVAL, "step3 must be 0, 1 or 2");
   GPN_CHECK(o.step3 != 2 || !ps.rowfft, GP_EUNSUPPORTED,
-            "the memory-lean step 3 runs with transform 1, 3 or 4, not the pruned row transforms");
+            "the memory-lean step 3 runs with transform 1 or 3, not the pruned row transforms");
   GPN_CHECK(o.step3 != 2 || !ddp, GP_EUNSUPPORTED, "GP_DF64 plans use the stored step-3 tensor (step3 = 1)");
   if (ddp) {
     ps.lean = false;
@@ -492,7 +489,6 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   plan->n_freq = ps.nfreq;
   plan->tr3 = ps.tr3;
   plan->rowfft = ps.rowfft;
-  plan->split3 = ps.split3;
   plan->lean = ps.lean;
   const long long a_bytes = ps.a_bytes;
   GPN_CHECK(o.max_bytes <= 0 || ps.est <= o.max_bytes, GP_ENOMEM,
@@ -973,7 +969,7 @@ int gp_plan_params(int d, long long N, double nu, double eps, double scale_min, 
     fill_hyper_info(ps.h, info);
     info->N = N;
     info->precision = o.precision;
-    info->transform = ps.tr3 ? 3 : (ps.rowfft ? 2 : (ps.split3 ? 4 : 1));
+    info->transform = ps.tr3 ? 3 : (ps.rowfft ? 2 : 1);
     info->bytes_resident = ps.est;
     info->max_rhs = o.max_rhs > 0 ? o.max_rhs : 1;
     info->rhs_block = (o.rhs_block > 0 && o.rhs_block < info->max_rhs) ? o.rhs_block : info->max_rhs;
@@ -1009,7 +1005,7 @@ int gp_plan_info_get(gp_plan_t plan, gp_plan_info* info) {
     info->upsampfac = h.upsamp;
     info->nufft_tol = h.nufft_tol;
     info->tile = h.tile;
-    info->transform = p->tr3 ? 3 : (p->rowfft ? 2 : (p->split3 ? 4 : 1));
+    info->transform = p->tr3 ? 3 : (p->rowfft ? 2 : 1);
     for (int q = 0; q < 3; ++q) {
       info->box_lo[q] = h.box_lo[q];
       info->box_hi[q] = h.box_hi[q];

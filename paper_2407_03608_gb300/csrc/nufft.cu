@@ -113,51 +113,9 @@ void build_a_tensor(Plan& plan, cudaStream_t st) {
     if (r_ != CUFFT_SUCCESS) ::gpn::fail(GP_ECUFFT, std::string(#call " failed: code ") + std::to_string((int)r_)); \
   } while (0)
 
-// Split full-grid transforms (d = 3): the last axis as one batch of 1-D real transforms
-// over every grid row, the first two as a strided 2-D complex transform over the half-
-// spectrum columns 0..M only.  Columns above M hold the last-axis transform alone after
-// the forward pass; step (3) sets them to zero with the rest of the spectrum outside the
-// mode box, so the inverse 2-D transform skips them and the 1-D C2R reads zeros there.
-// Same unnormalised result as the 3-D R2C/C2R on every mode the pipeline uses.
-namespace {
-cufftHandle make_rows_plan(const Plan& p, int R, bool forward) {
-  const long long nf = p.geom.nf, half = nf / 2 + 1;
-  long long n[1] = {nf};
-  long long in_emb[1] = {forward ? nf : half}, out_emb[1] = {forward ? half : nf};
-  const long long batch = (long long)p.geom.C * R * nf * nf;
-  cufftType t = p.precision == GP_FP32 ? (forward ? CUFFT_R2C : CUFFT_C2R) : (forward ? CUFFT_D2Z : CUFFT_Z2D);
-  cufftHandle hdl;
-  size_t work = 0;
-  GPN_CUFFT(cufftCreate(&hdl));
-  const cufftResult r = cufftMakePlanMany64(hdl, 1, n, in_emb, 1, in_emb[0], out_emb, 1, out_emb[0], t, batch, &work);
-  if (r != CUFFT_SUCCESS) {
-    cufftDestroy(hdl);
-    GPN_CUFFT(r);
-  }
-  return hdl;
-}
-}  // namespace
-
-cufftHandle Plan::yz_plan() {
-  if (fft_yz_made) return fft_yz;
-  const long long nf = geom.nf, half = nf / 2 + 1;
-  long long n[2] = {nf, nf}, emb[2] = {nf, nf};
-  size_t work = 0;
-  GPN_CUFFT(cufftCreate(&fft_yz));
-  const cufftResult r = cufftMakePlanMany64(fft_yz, 2, n, emb, half, 1, emb, half, 1,
-                                            precision == GP_FP32 ? CUFFT_C2C : CUFFT_Z2Z, geom.M + 1, &work);
-  if (r != CUFFT_SUCCESS) {
-    cufftDestroy(fft_yz);
-    GPN_CUFFT(r);
-  }
-  fft_yz_made = true;
-  return fft_yz;
-}
-
 cufftHandle Plan::fwd_plan(int R) {
   auto it = fft_fwd.find(R);
   if (it != fft_fwd.end()) return it->second;
-  if (split3) return fft_fwd[R] = make_rows_plan(*this, R, true);
   int n[3] = {(int)geom.nf, (int)geom.nf, (int)geom.nf};
   cufftHandle hdl;
   GPN_CUFFT(cufftPlanMany(&hdl, geom.d, n, nullptr, 1, 0, nullptr, 1, 0,
@@ -169,7 +127,6 @@ cufftHandle Plan::fwd_plan(int R) {
 cufftHandle Plan::inv_plan(int R) {
   auto it = fft_inv.find(R);
   if (it != fft_inv.end()) return it->second;
-  if (split3) return fft_inv[R] = make_rows_plan(*this, R, false);
   int n[3] = {(int)geom.nf, (int)geom.nf, (int)geom.nf};
   cufftHandle hdl;
   GPN_CUFFT(cufftPlanMany(&hdl, geom.d, n, nullptr, 1, 0, nullptr, 1, 0,
@@ -177,24 +134,6 @@ cufftHandle Plan::inv_plan(int R) {
   fft_inv[R] = hdl;
   return hdl;
 }
-
-namespace {
-// the strided 2-D transforms of the split path, one channel of one right-hand side at a time
-void run_yz(Plan& plan, int R, int dir, cudaStream_t st) {
-  cufftHandle h = plan.yz_plan();
-  GPN_CUFFT(cufftSetStream(h, st));
-  const long long S = plan.geom.nf * plan.geom.nf * (plan.geom.nf / 2 + 1);
-  for (long long q = 0; q < (long long)plan.geom.C * R; ++q) {
-    if (plan.precision == GP_FP32) {
-      cufftComplex* p = (cufftComplex*)plan.spec + q * S;
-      GPN_CUFFT(cufftExecC2C(h, p, p, dir));
-    } else {
-      cufftDoubleComplex* p = (cufftDoubleComplex*)plan.spec + q * S;
-      GPN_CUFFT(cufftExecZ2Z(h, p, p, dir));
-    }
-  }
-}
-}  // namespace
 
 void run_fft_forward(Plan& plan, int R, cudaStream_t st) {
   // the row-kernel paths mark between their rows and cuFFT's columns themselves
@@ -207,13 +146,11 @@ void run_fft_forward(Plan& plan, int R, cudaStream_t st) {
     GPN_CUFFT(cufftExecR2C(h, (cufftReal*)plan.grid, (cufftComplex*)plan.spec));
   else
     GPN_CUFFT(cufftExecD2Z(h, (cufftDoubleReal*)plan.grid, (cufftDoubleComplex*)plan.spec));
-  if (plan.split3) run_yz(plan, R, CUFFT_FORWARD, st);
 }
 
 void run_fft_inverse(Plan& plan, int R, cudaStream_t st) {
   if (plan.tr3) return tr3_inverse(plan, R, st);
   if (plan.rowfft) return rowfft_inverse(plan, R, st);
-  if (plan.split3) run_yz(plan, R, CUFFT_INVERSE, st);
   cufftHandle h = plan.inv_plan(R);
   GPN_CUFFT(cufftSetStream(h, st));
   if (plan.precision == GP_FP32)

@@ -132,13 +132,6 @@ struct Plan {
   double* stage_in = nullptr;           // staging for host-pointer calls, N * max_rhs
   double* stage_out = nullptr;
   std::map<int, cufftHandle> fft_fwd, fft_inv;  // keyed by R (full-grid path)
-  // split full-grid path (transform 4, d = 3): fft_fwd/fft_inv hold the last-axis
-  // R2C/C2R plans over every grid row; fft_yz the one strided 2-D C2C plan over the
-  // first two axes of the half-spectrum columns 0..M of one channel (used both ways)
-  bool split3 = false;
-  cufftHandle fft_yz = 0;
-  bool fft_yz_made = false;
-  cufftHandle yz_plan();
   // pruned transform path (d <= 2, power-of-two nf): compact spectra
   // [rows][C*R][M+1] and the data extent of the fine grid
   bool rowfft = false;
@@ -177,7 +170,7 @@ inline bool psi_tabulated(const Plan& p) { return psi_tabulated(p.geom.d, p.prec
 struct PlanShape {
   Hyper h;
   int C = 0;
-  bool tr3 = false, rowfft = false, lean = false, split3 = false;
+  bool tr3 = false, rowfft = false, lean = false;
   long long G = 0, S = 0, nfreq = 0;
   long long a_bytes = 0, lean_bytes = 0, est_rest = 0, est = 0;
 };

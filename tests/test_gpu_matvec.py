@@ -79,16 +79,14 @@ CASES = [
 
 @pytest.mark.parametrize("d,n,nu,n_t,n_sigma,M", CASES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("transform", [1, 2, 3, 4])
+@pytest.mark.parametrize("transform", [1, 2, 3])
 def test_matvec_vs_exact_nudft(gpn, d, n, nu, n_t, n_sigma, M, precision, transform):
     """transform 1: full-grid cuFFT R2C/C2R; 2: pruned row transforms (d <= 2);
-    3: pruned transposed transforms (d = 2); 4: split full-grid transforms (d = 3)."""
+    3: pruned transposed transforms (d = 2)."""
     if transform == 2 and d == 3:
         pytest.skip("pruned row transforms cover d <= 2")
     if transform == 3 and d != 2:
         pytest.skip("transposed transforms cover d = 2")
-    if transform == 4 and d != 3:
-        pytest.skip("split transforms cover d = 3")
     w = small_case(d, n, 0)
     X = w.points
     wp, sig = okern.paper_fields(w.s, w.l, d)
@@ -139,33 +137,6 @@ def test_pruned_transforms_match_full_grid(gpn, precision, transform):
         a = torch.from_numpy(gpinputs.random_alpha(w.N, 1, seed=seed)).cuda()
         e = rel(pruned.matvec(a).cpu().numpy(), full.matvec(a).cpu().numpy())
         assert e <= (1e-12 if precision == "fp64" else 2e-6), (seed, e)
-
-
-@pytest.mark.parametrize("eps", [1e-3, 1e-4])       # nf = 160 (2^5 * 5) and 256
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("step3", [1, 2])
-def test_split_3d_transforms_match_full_grid(gpn, eps, precision, step3):
-    """The split 3-D transforms (last axis as 1-D R2C/C2R, the first two as a strided 2-D
-    C2C over the half-spectrum columns 0..M) compute the same K~ alpha as the 3-D cuFFT
-    path, with the stored and the memory-lean step 3, over several right-hand sides and
-    repeated calls (the columns above M must come back as zeros every time)."""
-    w = gpinputs.config_3d(6000)
-    prec = gpn.GP_FP64 if precision == "fp64" else gpn.GP_FP32
-    full = gpn.Plan(w.points, w.s, w.l, nu=2.5, eps=eps, precision=prec, transform=1, step3=step3, max_rhs=2)
-    split = gpn.Plan(w.points, w.s, w.l, nu=2.5, eps=eps, precision=prec, transform=4, step3=step3, max_rhs=2,
-                     nf=full.info["nf"], **full.matched_opts())
-    assert split.info["transform"] == 4 and split.info["nf"] == full.info["nf"]
-    for seed in (41, 42):
-        a = torch.from_numpy(gpinputs.random_alpha(w.N, 2, seed=seed)).cuda()
-        e = rel(split.matvec(a).cpu().numpy(), full.matvec(a).cpu().numpy())
-        assert e <= (1e-12 if precision == "fp64" else 2e-6), (seed, e)
-
-
-def test_split_transforms_need_3d(gpn):
-    w = gpinputs.config_2d(500, 1.5)
-    with pytest.raises(gpn.GPError) as e:
-        gpn.Plan(w.points, w.s, w.l, nu=1.5, eps=1e-4, transform=4)
-    assert e.value.status == gpn.abi.GP_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("nf", [512, 8192])
