@@ -405,7 +405,15 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   const long long CR = (long long)C * grid_rhs;
   const long long spectra = (ps.tr3 || ps.rowfft) ? 3 * (d == 2 ? h.nf : 1) * CR * (h.M + 1) * 2 * (long long)rs
                                                   : CR * S * 2 * (long long)rs;
-  ps.est_rest = 2 * CR * G * (long long)rs + spectra + N * (long long)(d * (4 + rs) + 8 + C * rs) +
+  // full-grid transforms: each grid buffer holds a whole spectrum as well (cuFFT's work
+  // area of one transform direction lives in the buffer that direction leaves idle);
+  // cuFFT needs a work area as large as the spectrum unless nf is a power of two, and the
+  // inverse one gets its own allocation unless step 3 is memory-lean
+  const bool full = !ps.tr3 && !ps.rowfft;
+  const long long grid_pitch = full ? std::max(G, 2 * S) : G;
+  const bool pow2 = (h.nf & (h.nf - 1)) == 0;
+  const long long inv_work = (full && !pow2) ? CR * S * 2 * (long long)rs : 0;
+  ps.est_rest = 2 * CR * grid_pitch * (long long)rs + spectra + N * (long long)(d * (4 + rs) + 8 + C * rs) +
                 (long long)N * max_rhs * 8 * 9 +
                 (psi_tabulated(d, o.precision) ? N * (long long)d * h.width * (long long)rs : 0);
   // step 3: the stored tensor A' (1) or the memory-lean form from per-dimension
@@ -420,12 +428,12 @@ PlanShape plan_shape(int d, long long N, double nu, double eps, const gp_plan_op
   } else if (o.step3 == 2) {
     ps.lean = true;
   } else if (o.step3 == 0 && !ps.rowfft) {
-    const long long with_a = ps.est_rest + ps.a_bytes, with_f = ps.est_rest + ps.lean_bytes;
+    const long long with_a = ps.est_rest + ps.a_bytes + inv_work, with_f = ps.est_rest + ps.lean_bytes;
     const bool over_budget = o.max_bytes > 0 && with_a > o.max_bytes && with_f <= o.max_bytes;
     const bool over_free = free_b >= 0 && with_a > free_b && with_f <= free_b;
     ps.lean = over_budget || over_free;
   }
-  ps.est = ps.est_rest + (ps.lean ? ps.lean_bytes : ps.a_bytes);
+  ps.est = ps.est_rest + (ps.lean ? ps.lean_bytes : ps.a_bytes + inv_work);
   return ps;
 }
 
@@ -512,10 +520,13 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
     plan->a_tensor = plan->alloc((size_t)a_bytes);
     build_a_tensor(*plan, st);
   }
-  plan->grid = plan->alloc((size_t)C * grid_rhs * G * rs);
-  GPN_CUDA(cudaMemsetAsync(plan->grid, 0, (size_t)C * grid_rhs * G * rs, st));
-  plan->grid_out = plan->alloc((size_t)C * grid_rhs * G * rs);
-  GPN_CUDA(cudaMemsetAsync(plan->grid_out, 0, (size_t)C * grid_rhs * G * rs, st));
+  // full-grid transforms: room for a spectrum in each grid buffer (cuFFT work areas)
+  const long long grid_pitch = (!plan->tr3 && !plan->rowfft) ? std::max(G, 2 * S) : G;
+  plan->grid_bytes = (size_t)C * grid_rhs * grid_pitch * rs;
+  plan->grid = plan->alloc(plan->grid_bytes);
+  GPN_CUDA(cudaMemsetAsync(plan->grid, 0, plan->grid_bytes, st));
+  plan->grid_out = plan->alloc(plan->grid_bytes);
+  GPN_CUDA(cudaMemsetAsync(plan->grid_out, 0, plan->grid_bytes, st));
   if (plan->rowfft || plan->tr3) {
     set_data_extent(*plan);
     const size_t rows = d == 2 ? (size_t)h.nf : 1;
@@ -557,6 +568,9 @@ Plan* make_plan(const double* points, long long N, int d, const double* fa, cons
   } else if (plan->rowfft) {
     if (d == 2) plan->col_plan(1);
   } else {
+    // the widest batch first, so that the shared cuFFT work area is sized once
+    plan->fwd_plan(plan->grid_rhs);
+    plan->inv_plan(plan->grid_rhs);
     plan->fwd_plan(1);
     plan->inv_plan(1);
   }

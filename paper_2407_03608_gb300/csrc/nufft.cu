@@ -113,13 +113,56 @@ void build_a_tensor(Plan& plan, cudaStream_t st) {
     if (r_ != CUFFT_SUCCESS) ::gpn::fail(GP_ECUFFT, std::string(#call " failed: code ") + std::to_string((int)r_)); \
   } while (0)
 
+namespace {
+// A full-grid R2C or C2R plan over C * R grids.  Its cuFFT work area: for the forward
+// transform the interpolation grid (idle until the inverse rewrites every cell of it);
+// for the inverse, with the memory-lean step 3, the spreading grid (idle after the forward
+// transform; run_fft_inverse zeroes it again), else the plan's shared work allocation,
+// grown, with every inverse plan pointed at the larger one, when a plan needs more.
+cufftHandle make_full_plan(Plan& p, int R, bool forward) {
+  int n[3] = {(int)p.geom.nf, (int)p.geom.nf, (int)p.geom.nf};
+  const cufftType t = p.precision == GP_FP32 ? (forward ? CUFFT_R2C : CUFFT_C2R) : (forward ? CUFFT_D2Z : CUFFT_Z2D);
+  cufftHandle hdl;
+  GPN_CUFFT(cufftCreate(&hdl));
+  size_t ws = 0;
+  cufftResult r = cufftSetAutoAllocation(hdl, 0);
+  if (r == CUFFT_SUCCESS) r = cufftMakePlanMany(hdl, p.geom.d, n, nullptr, 1, 0, nullptr, 1, 0, t, p.geom.C * R, &ws);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(hdl);
+    GPN_CUFFT(r);
+  }
+  try {
+    if (ws > 0 && forward && ws <= p.grid_bytes) {
+      GPN_CUFFT(cufftSetWorkArea(hdl, p.grid_out));
+    } else if (ws > 0 && !forward && p.lean && ws <= p.grid_bytes) {
+      GPN_CUFFT(cufftSetWorkArea(hdl, p.grid));
+      p.inv_in_grid[R] = ws;
+    } else if (ws > 0) {
+      if (ws > p.fft_work_bytes) {
+        p.fft_work = p.alloc(ws);
+        p.fft_work_bytes = ws;
+        for (auto& kv : p.fft_inv)
+          if (!p.inv_in_grid.count(kv.first)) GPN_CUFFT(cufftSetWorkArea(kv.second, p.fft_work));
+        for (auto& kv : p.fft_fwd) {
+          size_t w = 0;
+          GPN_CUFFT(cufftGetSize(kv.second, &w));
+          if (w > p.grid_bytes) GPN_CUFFT(cufftSetWorkArea(kv.second, p.fft_work));
+        }
+      }
+      GPN_CUFFT(cufftSetWorkArea(hdl, p.fft_work));
+    }
+  } catch (...) {
+    cufftDestroy(hdl);
+    throw;
+  }
+  return hdl;
+}
+}  // namespace
+
 cufftHandle Plan::fwd_plan(int R) {
   auto it = fft_fwd.find(R);
   if (it != fft_fwd.end()) return it->second;
-  int n[3] = {(int)geom.nf, (int)geom.nf, (int)geom.nf};
-  cufftHandle hdl;
-  GPN_CUFFT(cufftPlanMany(&hdl, geom.d, n, nullptr, 1, 0, nullptr, 1, 0,
-                          precision == GP_FP32 ? CUFFT_R2C : CUFFT_D2Z, geom.C * R));
+  const cufftHandle hdl = make_full_plan(*this, R, true);
   fft_fwd[R] = hdl;
   return hdl;
 }
@@ -127,10 +170,7 @@ cufftHandle Plan::fwd_plan(int R) {
 cufftHandle Plan::inv_plan(int R) {
   auto it = fft_inv.find(R);
   if (it != fft_inv.end()) return it->second;
-  int n[3] = {(int)geom.nf, (int)geom.nf, (int)geom.nf};
-  cufftHandle hdl;
-  GPN_CUFFT(cufftPlanMany(&hdl, geom.d, n, nullptr, 1, 0, nullptr, 1, 0,
-                          precision == GP_FP32 ? CUFFT_C2R : CUFFT_Z2D, geom.C * R));
+  const cufftHandle hdl = make_full_plan(*this, R, false);
   fft_inv[R] = hdl;
   return hdl;
 }
@@ -157,6 +197,8 @@ void run_fft_inverse(Plan& plan, int R, cudaStream_t st) {
     GPN_CUFFT(cufftExecC2R(h, (cufftComplex*)plan.spec, (cufftReal*)plan.grid_out));
   else
     GPN_CUFFT(cufftExecZ2D(h, (cufftDoubleComplex*)plan.spec, (cufftDoubleReal*)plan.grid_out));
+  const auto in_grid = plan.inv_in_grid.find(R);
+  if (in_grid != plan.inv_in_grid.end()) GPN_CUDA(cudaMemsetAsync(plan.grid, 0, in_grid->second, st));
   prof_mark(plan, 1, st);
 }
 

@@ -132,6 +132,15 @@ struct Plan {
   double* stage_in = nullptr;           // staging for host-pointer calls, N * max_rhs
   double* stage_out = nullptr;
   std::map<int, cufftHandle> fft_fwd, fft_inv;  // keyed by R (full-grid path)
+  // cuFFT work areas of the full-grid plans (cuFFT's own allocation would give every
+  // plan one, as large as a spectrum when nf is not a power of two): the forward
+  // transforms work in grid_out, which the inverse rewrites whole afterwards; the inverse
+  // ones in one shared allocation, or, with the memory-lean step 3, in the spreading grid,
+  // zeroed again after the transform (the spread writes only the tiles points reach)
+  size_t grid_bytes = 0;                // allocation of grid and of grid_out
+  void* fft_work = nullptr;
+  size_t fft_work_bytes = 0;
+  std::map<int, size_t> inv_in_grid;    // R -> bytes of the spreading grid an inverse plan works in
   // pruned transform path (d <= 2, power-of-two nf): compact spectra
   // [rows][C*R][M+1] and the data extent of the fine grid
   bool rowfft = false;
