@@ -286,10 +286,11 @@ constexpr int reg_channels(int C) { return C <= 16 ? C : 32; }
 
 template <typename T>
 constexpr int rows_per_warp(int nc) {
-  // float64 sums take two registers each: two rows a warp; float and float-float keep four
-  // (float-float sums are two floats, and the longer band halves the tiles a point visits,
-  // each visit evaluating its kernel values)
-  return ((sizeof(T) == 8 && !is_dd<T>::value) || nc > 16) ? 2 : 4;
+  // float64 and float-float sums take two registers each: two rows a warp (four rows of
+  // float-float sums held 156 registers at 9 channels, one CTA an SM, and the spread ran
+  // 4.29 ms at the 2-D benchmark size against 3.14 ms with two rows and 80 registers);
+  // FP32 keeps four
+  return (sizeof(T) == 8 || nc > 16) ? 2 : 4;
 }
 
 size_t smem_bytes(size_t rs, int nc, int rpw, int w) {
