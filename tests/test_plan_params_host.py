@@ -255,3 +255,25 @@ def test_rhs_block_keeps_one_block_of_grids(abi):
     assert blocked["bytes_resident"] - eight["bytes_resident"] == 100_000 * 56 * 8 * 9
     # a block at least max_rhs is no block
     assert params(abi, 2, 100_000, 1e-5, 0.01, 0.02, max_rhs=4, rhs_block=9)["rhs_block"] == 4
+
+
+@pytest.mark.parametrize("nf", [864, 1024])
+def test_full_grid_footprint_counts_the_cufft_work_area(abi, nf):
+    """3-D full-grid plans: cuFFT's transforms need a work area as large as the half
+    spectrum when nf is not a power of two.  The forward one works in the interpolation
+    grid and the inverse, with the memory-lean step 3, in the spreading grid, so the
+    footprint adds a spectrum only for the stored-A' plan at nf = 864; each grid buffer
+    holds max(nf^3, 2 S) reals either way."""
+    N, rs = 200_000, 4
+    full = params(abi, 3, N, 1e-5, 0.03, 0.06, nu=2.5, step3=1, nf=nf, set=abi.GP_SET_NF)
+    lean = params(abi, 3, N, 1e-5, 0.03, 0.06, nu=2.5, step3=2, nf=nf, set=abi.GP_SET_NF)
+    assert full["nf"] == lean["nf"] == nf and full["step3"] == 1 and lean["step3"] == 2
+    C, M, J = full["n_sigma"] + 1, full["M"], full["n_t"] + 1
+    S = nf * nf * (nf // 2 + 1)
+    a_bytes = C * (C + 1) // 2 * (2 * M + 1) ** 2 * (M + 1) * rs
+    lean_bytes = J * (M + 1) * (-(-C // (16 // rs)) * (16 // rs)) * rs
+    work = C * S * 2 * rs if nf & (nf - 1) else 0
+    assert full["bytes_resident"] - lean["bytes_resident"] == a_bytes - lean_bytes + work
+    # the grid padding: two buffers of C max(nf^3, 2 S) reals against C nf^3 each
+    plain = params(abi, 3, N, 1e-5, 0.03, 0.06, nu=2.5, step3=2, nf=nf, set=abi.GP_SET_NF, max_rhs=2)
+    assert plain["bytes_resident"] - lean["bytes_resident"] >= 2 * C * max(nf ** 3, 2 * S) * rs
