@@ -600,8 +600,71 @@ __global__ void __launch_bounds__(128) k_diag_t(DiagTArgs<T> a) {
   }
 }
 
+// 8-byte async copy global -> shared (no registers), completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// k_diag_t for float-float plans with up to 9 channels: the C(C+1)/2 entries of A' at the
+// thread's frequency go to shared memory by asynchronous copies (one column of
+// s_av per thread, so a warp's reads are consecutive) instead of registers, which keeps
+// the thread at about 100 registers and four CTAs an SM; the entries are then read once
+// per (k, l) like the register form reads them.
+constexpr int kDiagDDMaxC = 9;
+constexpr int kDiagThreads = 128;
+template <int NC>
+__global__ void __launch_bounds__(kDiagThreads, 4) k_diag_t_dd(DiagTArgs<dd> a) {
+  constexpr int NP = NC * (NC + 1) / 2;
+  __shared__ dd s_av[NP][kDiagThreads];
+  const int n1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (n1 > a.M) return;   // no barrier below: each thread reads only its own column
+  const size_t Mp = (size_t)a.M + 1;
+  const size_t colstride = Mp * a.nf;
+  const size_t off_p = (size_t)m * a.nf + n1;
+  const size_t off_n = (size_t)m * a.nf + (n1 == 0 ? 0 : a.nf - n1);
+  const dd* Am = a.A + (size_t)m * Mp + n1;
+  const size_t pstride = Mp * Mp;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) cp_async8(&s_av[p][threadIdx.x], Am + (size_t)p * pstride);
+  for (int r = 0; r < a.R; ++r) {
+    const cpx<dd>* Yr = a.Y + (size_t)r * NC * colstride;
+    cpx<dd>* Zr = a.Z + (size_t)r * NC * colstride;
+    cpx<dd> bp[NC], bn[NC];
+#pragma unroll
+    for (int l = 0; l < NC; ++l) {
+      bp[l] = Yr[l * colstride + off_p];
+      bn[l] = Yr[l * colstride + off_n];
+    }
+    if (r == 0) cp_async_wait_all();
+#pragma unroll 1
+    for (int k = 0; k < NC; ++k) {
+      cpx<dd> ap{dd(0), dd(0)}, an{dd(0), dd(0)};
+#pragma unroll
+      for (int l = 0; l < NC; ++l) {
+        const int lo = k < l ? k : l, hi = k < l ? l : k;
+        const dd w = s_av[lo * NC - lo * (lo - 1) / 2 + (hi - lo)][threadIdx.x];
+        madd_lazy(ap.x, w, bp[l].x);
+        madd_lazy(ap.y, w, bp[l].y);
+        madd_lazy(an.x, w, bn[l].x);
+        madd_lazy(an.y, w, bn[l].y);
+      }
+      Zr[k * colstride + off_p] = {renorm_val(ap.x), renorm_val(ap.y)};
+      if (n1 != 0) Zr[k * colstride + off_n] = {renorm_val(an.x), renorm_val(an.y)};
+    }
+  }
+}
+
 template <typename T, int NC>
 void diag_dispatch(const DiagTArgs<T>& a, cudaStream_t st) {
+  if constexpr (is_dd<T>::value && NC <= kDiagDDMaxC) {
+    if (a.C == NC) {
+      dim3 grid((unsigned)((a.M + kDiagThreads) / kDiagThreads), (unsigned)(a.M + 1));
+      k_diag_t_dd<NC><<<grid, kDiagThreads, 0, st>>>(a);
+      return;
+    }
+  }
   if constexpr (NC > 16) {
     dim3 grid((unsigned)((a.M + 128) / 128), (unsigned)(a.M + 1));
     k_diag_t<T, 32><<<grid, 128, 0, st>>>(a);
