@@ -152,7 +152,9 @@ typedef struct gp_plan_opts {
                              time (float64, about 12 bytes each, not in the footprint
                              estimate) and applied in every matvec and solve on the plan's
                              points, not to posterior means.  Meant for sparse point sets: the
-                             cost grows with the number of pairs.  0 (default): off.     */
+                             cost grows with the number of pairs.  GP_ENOMEM when the factor
+                             tables would pass 16 GB or the pairs 2^31 - 1; GP_EINVAL when
+                             negative or not finite.  0 (default): off.                  */
 } gp_plan_opts;
 
 typedef struct gp_plan_info {
