@@ -22,6 +22,7 @@
 // frequencies up to M dw is exact to about 2e-12 of its size), then read per pair.
 #include <cub/cub.cuh>
 
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -297,6 +298,16 @@ void build_near_field(Plan& plan, double radius, const double* x_dev, const doub
   const unsigned nb = (unsigned)((n + 127) / 128);
   k_near_pairs<<<nb, 128, 0, st>>>(a);
   GPN_CUDA(cudaGetLastError());
+  // the total in 64 bits first: the row offsets are ints
+  {
+    std::vector<int> counts((size_t)n);
+    GPN_CUDA(cudaMemcpyAsync(counts.data(), ptr, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    GPN_CUDA(cudaStreamSynchronize(st));
+    long long sum = 0;
+    for (int c : counts) sum += c;
+    GPN_CHECK(sum <= (long long)INT_MAX, GP_ENOMEM,
+              std::to_string(sum) + " near-field pairs: more than the int row offsets hold; take a smaller near_radius");
+  }
   // exclusive scan of the counts into the row offsets (the last entry is the total)
   GPN_CUDA(cudaMemsetAsync(ptr + n, 0, sizeof(int), st));
   size_t tmp_bytes = 0;
@@ -309,7 +320,6 @@ void build_near_field(Plan& plan, double radius, const double* x_dev, const doub
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(tmp);
   GPN_CUDA(e);
-  GPN_CHECK(total >= 0, GP_ENOMEM, "more near-field pairs than an int can count: take a smaller near_radius");
   plan.near_ptr = ptr;
   plan.near_nnz = total;
   plan.near_col = (int*)plan.alloc(sizeof(int) * (size_t)std::max(total, 1));
